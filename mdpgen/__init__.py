@@ -1,0 +1,254 @@
+"""Seeded synthetic MDP generators shared by the tests, the benchmark and the oracle checks.
+
+This module only draws problem data (transition rows, costs, start values, policies).  It holds
+none of the mini-batch operator's arithmetic, so both the CUDA path and the FP64 oracle can take
+their inputs from it without sharing any of the method.
+
+Every array is drawn in FP64 from ``numpy.random.Generator(PCG64(seed))`` and rounded to FP32
+(int32 for successor indices, int64 for CSR row pointers).  The FP32-rounded arrays *are* the
+problem: the oracle promotes them exactly to FP64 and never renormalises them.
+
+Layout (shared with the C-ABI): row ``r = s*m + a`` holds P(.|s,a).
+  dense: ``P[n, m, n]`` float32, row-major, so the m rows of a state are contiguous;
+  CSR:   ``row_ptr[n*m+1]`` int64, ``col[nnz]`` int32 (sorted within a row), ``prob[nnz]`` float32;
+  both:  ``cost[n*m]`` float32, ``+inf`` marks an inadmissible action (the paper's U(i), Sec. II-A).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+__all__ = [
+    "MDP", "dense_dirichlet", "csr_uniform_k", "batched_uneven", "random_values",
+    "random_policy", "config1", "config2", "config3", "config4", "config5", "csr_ragged",
+]
+
+
+@dataclasses.dataclass
+class MDP:
+    """A finite discounted MDP (S, U, P, g, alpha) of Sec. II-A with n states and m actions."""
+    n: int
+    m: int
+    gamma: float
+    fmt: str                                   # "dense" | "csr"
+    cost: np.ndarray                           # float32 [n*m]
+    P: Optional[np.ndarray] = None             # float32 [n, m, n] (dense)
+    row_ptr: Optional[np.ndarray] = None       # int64 [n*m+1] (csr)
+    col: Optional[np.ndarray] = None           # int32 [nnz] (csr)
+    prob: Optional[np.ndarray] = None          # float32 [nnz] (csr)
+    logits: Optional[np.ndarray] = None        # float32 [nnz] when prob = softmax(logits)
+    name: str = ""
+
+    @property
+    def nnz(self) -> int:
+        return int(self.n) * self.m * int(self.n) if self.fmt == "dense" else int(self.row_ptr[-1])
+
+    def p_bytes(self) -> int:
+        """Bytes of transition data (probabilities + indices) one full pass over all rows reads."""
+        if self.fmt == "dense":
+            return self.P.nbytes
+        return self.prob.nbytes + self.col.nbytes
+
+    def uniform_k(self) -> int:
+        """Successors per row if every CSR row has the same length, else 0."""
+        if self.fmt != "csr":
+            return 0
+        rows = self.n * self.m
+        k = int(self.row_ptr[-1]) // rows if rows else 0
+        if k * rows != int(self.row_ptr[-1]):
+            return 0
+        if not np.array_equal(self.row_ptr, np.arange(rows + 1, dtype=np.int64) * k):
+            return 0
+        return k
+
+
+def _rng(seed) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _costs(rng, rows, dist):
+    if dist == "uniform":
+        return rng.random(rows).astype(np.float32)
+    if dist == "normal":
+        return rng.standard_normal(rows).astype(np.float32)
+    raise ValueError(dist)
+
+
+def dense_dirichlet(n: int, m: int, alpha: float = 1.0, gamma: float = 0.95, seed: int = 0,
+                    cost_dist: str = "uniform", block_rows: int = 4096, name: str = "") -> MDP:
+    """Dense rows P(.|s,a) ~ Dirichlet(alpha) over all n states (normalised Gamma(alpha) draws).
+
+    Rows are drawn blockwise from independent child seeds so memory stays bounded at large n.
+    """
+    rows = n * m
+    ss = np.random.SeedSequence(seed)
+    c_seq, p_seq = ss.spawn(2)
+    cost = _costs(_rng(c_seq), rows, cost_dist)
+    P = np.empty((rows, n), dtype=np.float32)
+    nblk = (rows + block_rows - 1) // block_rows
+    for bi, child in enumerate(p_seq.spawn(nblk)):
+        r0, r1 = bi * block_rows, min(rows, (bi + 1) * block_rows)
+        g = _rng(child)
+        if alpha == 1.0:
+            x = g.standard_exponential((r1 - r0, n))
+        else:
+            x = g.standard_gamma(alpha, (r1 - r0, n))
+        s = x.sum(axis=1, keepdims=True)
+        # a Gamma(alpha<1) row can underflow to all-zeros only for absurdly small n*alpha; guard anyway
+        bad = (s[:, 0] <= 0)
+        if bad.any():
+            x[bad, 0] = 1.0
+            s = x.sum(axis=1, keepdims=True)
+        P[r0:r1] = (x / s).astype(np.float32)
+    return MDP(n=n, m=m, gamma=gamma, fmt="dense", cost=cost, P=P.reshape(n, m, n), name=name)
+
+
+def _distinct_sorted(g: np.random.Generator, rows: int, n: int, k: int) -> np.ndarray:
+    """k distinct successors per row, uniform without replacement, sorted ascending."""
+    if k > n:
+        raise ValueError("k > n")
+    if k * 4 >= n:
+        # dense regime: a per-row permutation prefix
+        out = np.empty((rows, k), dtype=np.int32)
+        for r in range(rows):
+            out[r] = np.sort(g.permutation(n)[:k])
+        return out
+    idx = g.integers(0, n, size=(rows, k), dtype=np.int32)
+    idx.sort(axis=1)
+    while True:
+        dup = (np.diff(idx, axis=1) == 0).any(axis=1)
+        nd = int(dup.sum())
+        if nd == 0:
+            return idx
+        fix = g.integers(0, n, size=(nd, k), dtype=np.int32)
+        fix.sort(axis=1)
+        idx[dup] = fix
+
+
+def csr_uniform_k(n: int, m: int, k: int, gamma: float = 0.99, seed: int = 0,
+                  prob_kind: str = "dirichlet1", cost_dist: str = "uniform",
+                  block_rows: int = 1 << 20, name: str = "") -> MDP:
+    """CSR MDP: every (s,a) row has k distinct successors drawn uniformly without replacement.
+
+    prob_kind "dirichlet1": probabilities ~ Dirichlet(1) (normalised Exp(1));
+    prob_kind "softmax":    probabilities = softmax of N(0,1) logits (logits are returned too).
+    """
+    rows = n * m
+    nnz = rows * k
+    ss = np.random.SeedSequence(seed)
+    c_seq, p_seq = ss.spawn(2)
+    cost = _costs(_rng(c_seq), rows, cost_dist)
+    col = np.empty(nnz, dtype=np.int32)
+    prob = np.empty(nnz, dtype=np.float32)
+    logits = np.empty(nnz, dtype=np.float32) if prob_kind == "softmax" else None
+    nblk = (rows + block_rows - 1) // block_rows
+    for bi, child in enumerate(p_seq.spawn(nblk)):
+        r0, r1 = bi * block_rows, min(rows, (bi + 1) * block_rows)
+        g = _rng(child)
+        idx = _distinct_sorted(g, r1 - r0, n, k)
+        col[r0 * k:r1 * k] = idx.reshape(-1)
+        if prob_kind == "dirichlet1":
+            x = g.standard_exponential((r1 - r0, k))
+            p = x / x.sum(axis=1, keepdims=True)
+        elif prob_kind == "softmax":
+            z = g.standard_normal((r1 - r0, k))
+            logits[r0 * k:r1 * k] = z.astype(np.float32).reshape(-1)
+            z32 = z.astype(np.float32).astype(np.float64)   # the logits the problem actually holds
+            e = np.exp(z32 - z32.max(axis=1, keepdims=True))
+            p = e / e.sum(axis=1, keepdims=True)
+        else:
+            raise ValueError(prob_kind)
+        prob[r0 * k:r1 * k] = p.astype(np.float32).reshape(-1)
+    row_ptr = np.arange(rows + 1, dtype=np.int64) * k
+    return MDP(n=n, m=m, gamma=gamma, fmt="csr", cost=cost, row_ptr=row_ptr, col=col,
+               prob=prob, logits=logits, name=name)
+
+
+def csr_ragged(n: int, m: int, kmax: int, gamma: float = 0.9, seed: int = 0,
+               inadmissible_frac: float = 0.0, name: str = "") -> MDP:
+    """CSR MDP with row lengths uniform in {1..kmax} (ragged rows exercise the generic row path).
+
+    A fraction of (s,a) pairs gets cost +inf (inadmissible); action 0 always stays admissible so
+    every U(i) is nonempty (Sec. II-A).
+    """
+    g = _rng(seed)
+    rows = n * m
+    lens = g.integers(1, kmax + 1, size=rows).astype(np.int64)
+    lens = np.minimum(lens, n)
+    row_ptr = np.zeros(rows + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    col = np.empty(int(row_ptr[-1]), dtype=np.int32)
+    prob = np.empty(int(row_ptr[-1]), dtype=np.float32)
+    for r in range(rows):
+        L = int(lens[r])
+        c = np.sort(g.choice(n, size=L, replace=False)).astype(np.int32)
+        x = g.standard_exponential(L)
+        col[row_ptr[r]:row_ptr[r + 1]] = c
+        prob[row_ptr[r]:row_ptr[r + 1]] = (x / x.sum()).astype(np.float32)
+    cost = g.random(rows).astype(np.float32)
+    if inadmissible_frac > 0:
+        mask = g.random(rows) < inadmissible_frac
+        mask[0::m] = False
+        cost[mask] = np.inf
+    return MDP(n=n, m=m, gamma=gamma, fmt="csr", cost=cost, row_ptr=row_ptr, col=col,
+               prob=prob, name=name)
+
+
+def random_values(n: int, seed: int = 0, scale: float = 1.0, offset: float = 0.0) -> np.ndarray:
+    """A seeded FP32 value vector (start values / test functions J)."""
+    return (offset + scale * _rng(seed).standard_normal(n)).astype(np.float32)
+
+
+def random_policy(n: int, m: int, seed: int = 0) -> np.ndarray:
+    return _rng(seed).integers(0, m, size=n, dtype=np.int32)
+
+
+# ---------------------------------------------------------------------------------------------
+# The five benchmark workloads (synthetic stand-ins; MDP seeds 0..4, permutation seed 12345).
+# Each takes optional size overrides so tests can build the same shapes at small sizes.
+# ---------------------------------------------------------------------------------------------
+PERM_SEED = 12345
+
+
+def config1(n: int = 500, m: int = 4, seed: int = 0) -> MDP:
+    """Dense n=500, m=4, Dirichlet(1) rows over all states, c ~ U[0,1], gamma=0.95 (b=50)."""
+    return dense_dirichlet(n, m, alpha=1.0, gamma=0.95, seed=seed, name=f"dense-dirichlet1-n{n}-m{m}")
+
+
+def config2(n: int = 1 << 20, m: int = 8, k: int = 32, seed: int = 1) -> MDP:
+    """CSR n=2^20, m=8, k=32 distinct uniform successors, Dirichlet(1), c ~ U[0,1], gamma=0.99."""
+    return csr_uniform_k(n, m, k, gamma=0.99, seed=seed, name=f"csr-k{k}-n{n}-m{m}")
+
+
+def config3(count: int = 256, nmin: int = 256, nmax: int = 65536, k: int = 16, seed: int = 2) -> List[MDP]:
+    """256 CSR MDPs: n log-uniform in [256, 65536], m ~ U{2..16}, k=16, gamma ~ U[0.9, 0.99]."""
+    return batched_uneven(count, nmin, nmax, k, seed)
+
+
+def batched_uneven(count: int, nmin: int, nmax: int, k: int, seed: int) -> List[MDP]:
+    g = _rng(seed)
+    ns = np.floor(np.exp(g.uniform(math.log(nmin), math.log(nmax), size=count))).astype(np.int64)
+    ms = g.integers(2, 17, size=count)
+    gammas = g.uniform(0.9, 0.99, size=count)
+    seeds = np.random.SeedSequence(seed).spawn(count)
+    out = []
+    for i in range(count):
+        n_i = int(max(ns[i], k))
+        out.append(csr_uniform_k(n_i, int(ms[i]), k, gamma=float(gammas[i]), seed=seeds[i],
+                                 name=f"batched-{i}"))
+    return out
+
+
+def config4(n: int = 16384, m: int = 16, seed: int = 3) -> MDP:
+    """Dense n=16384, m=16, Dirichlet(0.1) rows (peaked), c ~ N(0,1), gamma=0.999."""
+    return dense_dirichlet(n, m, alpha=0.1, gamma=0.999, seed=seed, cost_dist="normal",
+                           name=f"dense-dirichlet0.1-n{n}-m{m}")
+
+
+def config5(n: int = 65536, m: int = 8, k: int = 16, seed: int = 4) -> MDP:
+    """CSR n=65536, m=8, k=16, P = softmax(N(0,1) logits), c ~ U[0,1], gamma=0.95."""
+    return csr_uniform_k(n, m, k, gamma=0.95, seed=seed, prob_kind="softmax",
+                         name=f"csr-softmax-k{k}-n{n}-m{m}")

@@ -1,0 +1,114 @@
+"""Closed forms that pin the iterative oracle (TEST INFRASTRUCTURE ONLY).
+
+* ``policy_value``: J_mu from the Bellman equation for mu (eq. (4)) as the linear system
+  (I - alpha P_mu) J = g_mu, solved directly (LAPACK / SuperLU) or, for large sparse chains,
+  by GMRES to a 1e-14 relative residual (the system's inf-norm condition is <= (1+alpha)/(1-alpha)).
+* ``brute_force``: J* = min over all deterministic stationary policies of J_mu (eq. (2)), by
+  enumeration on tiny problems (m^n policies).
+* ``policy_iteration``: exact PI (Sec. II-C) with direct solves, ending when the greedy policy of
+  J_mu is mu itself; its result is certified by one Bellman pass (J = TJ, eq. (5)).
+
+Everything here is numpy/scipy FP64 and is independent of ``oracle.c``.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+
+def _rows(mdp, pi):
+    return np.arange(mdp.n, dtype=np.int64) * mdp.m + np.asarray(pi, dtype=np.int64)
+
+
+def policy_matrix(mdp, pi):
+    """(P_mu, g_mu): the transition matrix and stage costs under the policy mu = pi."""
+    rows = _rows(mdp, pi)
+    g = mdp.cost.astype(np.float64)[rows]
+    if mdp.fmt == "dense":
+        Pm = mdp.P.reshape(mdp.n * mdp.m, mdp.n)[rows].astype(np.float64)
+        return Pm, g
+    rp = mdp.row_ptr
+    starts, ends = rp[rows], rp[rows + 1]
+    lens = ends - starts
+    idx = np.concatenate([np.arange(a, b) for a, b in zip(starts, ends)]) if len(rows) else np.zeros(0, np.int64)
+    indptr = np.zeros(mdp.n + 1, dtype=np.int64)
+    np.cumsum(lens, out=indptr[1:])
+    Pm = sp.csr_matrix((mdp.prob[idx].astype(np.float64), mdp.col[idx].astype(np.int64), indptr),
+                       shape=(mdp.n, mdp.n))
+    return Pm, g
+
+
+def policy_value(mdp, pi, method: str = "auto"):
+    """Exact J_mu = (I - alpha P_mu)^{-1} g_mu (eq. (4))."""
+    Pm, g = policy_matrix(mdp, pi)
+    if np.isinf(g).any():
+        raise ValueError("policy uses an inadmissible action")
+    n = mdp.n
+    a = float(mdp.gamma)
+    if sp.issparse(Pm):
+        A = (sp.identity(n, format="csr") - a * Pm).tocsc()
+        if method == "gmres" or (method == "auto" and n > 20000):
+            x, info = spla.gmres(A, g, rtol=1e-14, atol=0.0, restart=200, maxiter=10000)
+            if info != 0:
+                raise RuntimeError(f"gmres did not converge (info={info})")
+            return x
+        return spla.spsolve(A, g)
+    A = np.eye(n) - a * Pm
+    return np.linalg.solve(A, g)
+
+
+def bellman_pass(mdp, J):
+    """Vectorised Bellman pass (eq. (7)): returns (TJ, greedy policy, Q-gap, Q[n,m])."""
+    J = np.asarray(J, dtype=np.float64)
+    c = mdp.cost.astype(np.float64).reshape(mdp.n, mdp.m)
+    if mdp.fmt == "dense":
+        PJ = mdp.P.reshape(mdp.n * mdp.m, mdp.n).astype(np.float64) @ J
+    else:
+        A = sp.csr_matrix((mdp.prob.astype(np.float64), mdp.col.astype(np.int64), mdp.row_ptr),
+                          shape=(mdp.n * mdp.m, mdp.n))
+        PJ = A @ J
+    Q = c + mdp.gamma * PJ.reshape(mdp.n, mdp.m)
+    Q = np.where(np.isinf(c), np.inf, Q)
+    order = np.argsort(Q, axis=1, kind="stable")
+    pi = order[:, 0].astype(np.int32)
+    TJ = Q[np.arange(mdp.n), pi]
+    if mdp.m > 1:
+        gap = Q[np.arange(mdp.n), order[:, 1]] - TJ
+    else:
+        gap = np.full(mdp.n, np.inf)
+    return TJ, pi, gap, Q
+
+
+def brute_force(mdp):
+    """J* by enumerating every admissible deterministic policy (tiny problems only)."""
+    n, m = mdp.n, mdp.m
+    if m ** n > 20000:
+        raise ValueError("too many policies for brute force")
+    c = mdp.cost.reshape(n, m)
+    best = np.full(n, np.inf)
+    for pol in itertools.product(range(m), repeat=n):
+        pi = np.array(pol, dtype=np.int32)
+        if np.isinf(c[np.arange(n), pi]).any():
+            continue
+        J = policy_value(mdp, pi)
+        best = np.minimum(best, J)
+    return best
+
+
+def policy_iteration(mdp, max_iters: int = 200):
+    """Exact PI with direct solves; returns (J*, pi*, ||T J* - J*||_inf)."""
+    c = mdp.cost.reshape(mdp.n, mdp.m)
+    pi = np.argmin(np.where(np.isinf(c), np.inf, c), axis=1).astype(np.int32)
+    for _ in range(max_iters):
+        J = policy_value(mdp, pi)
+        TJ, new_pi, gap, Q = bellman_pass(mdp, J)
+        # keep the current action on exact ties so PI terminates
+        keep = Q[np.arange(mdp.n), pi] <= TJ
+        new_pi = np.where(keep, pi, new_pi).astype(np.int32)
+        if np.array_equal(new_pi, pi):
+            return J, pi, float(np.max(np.abs(TJ - J)))
+        pi = new_pi
+    raise RuntimeError("policy iteration did not terminate")

@@ -1,0 +1,387 @@
+"""Pins for the FP64 oracle: each checks it against something other than itself.
+
+* Philox4x32-10 against published known-answer vectors (tests/golden/philox4x32_10_kat.txt);
+* the permutation: bijection, independence from b, uniform position of a state;
+* a hand-derived closed form (tests/golden/two_state_closed_form.txt);
+* brute force over every deterministic policy with direct solves (eq. (2), eq. (4));
+* the set-based definition of M_b(i) and B_b (eqs. (10)-(12)) evaluated literally;
+* the b=n (Bellman, eq. (7)) and b=1 (Gauss-Seidel, Sec. II-D) reductions (Sec. III-A);
+* monotonicity, shift invariance, alpha-contraction, fixed point (Sec. III-B.1);
+* the batch-size comparison theorem and corollary (Sec. III-B.2) on divisor chains;
+* MB-MPI (Alg. 1) against exact policy iteration; the stopping error bound.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import mdpgen
+import oracle
+from oracle import exact
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------------------------------------
+def test_philox_known_answers():
+    n = 0
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        v = [int(x, 16) for x in line.split()]
+        out = oracle.philox4x32_10(v[:4], v[4:6])
+        assert list(int(x) for x in out) == v[6:]
+        n += 1
+    assert n == 3
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 16, 17, 500, 1000, 4097, 65536, 99991])
+def test_perm_is_bijection(n):
+    for sweep in (0, 1, 12345678901):
+        p = oracle.perm(n, 12345, sweep)
+        assert np.array_equal(np.sort(p), np.arange(n))
+
+
+def test_perm_large_bijection_and_sweeps_differ():
+    n = 1 << 20
+    a = oracle.perm(n, 12345, 0)
+    b = oracle.perm(n, 12345, 1)
+    assert np.array_equal(np.sort(a), np.arange(n))
+    assert not np.array_equal(a, b)
+    # a random bijection has about one fixed point
+    assert np.sum(a == np.arange(n)) < 20
+
+
+def test_perm_matches_single_evaluation_and_seed_matters():
+    n = 777
+    p = oracle.perm(n, 99, 5)
+    for pos in (0, 1, 100, 776):
+        assert oracle.perm_at(n, 99, 5, pos) == p[pos]
+    assert not np.array_equal(p, oracle.perm(n, 100, 5))
+
+
+def test_perm_uniform_position():
+    """Chi-square: the position of a fixed state over many seeds is uniform on [0, n)."""
+    n, trials = 10, 20000
+    counts = np.zeros(n)
+    for seed in range(trials):
+        p = oracle.perm(n, seed, 3)
+        counts[int(np.nonzero(p == 3)[0][0])] += 1
+    e = trials / n
+    chi2 = float(((counts - e) ** 2 / e).sum())
+    assert chi2 < 27.88  # 99.9% quantile of chi-square with 9 dof
+
+
+def test_perm_half_bits():
+    assert oracle.perm_half_bits(1) == 1
+    assert oracle.perm_half_bits(2) == 1
+    assert oracle.perm_half_bits(4) == 1
+    assert oracle.perm_half_bits(5) == 2
+    assert oracle.perm_half_bits(500) == 5
+    assert oracle.perm_half_bits(1 << 20) == 10
+    assert oracle.perm_half_bits((1 << 20) + 1) == 11
+
+
+# ------------------------------------------------------------------------------------------------
+def _golden_two_state():
+    rows, meta = {}, {}
+    for line in open(os.path.join(GOLDEN, "two_state_closed_form.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        t = line.split()
+        if t[0] == "row":
+            rows[(int(t[1]), int(t[2]))] = (float(t[3]), [float(x) for x in t[4:]])
+        else:
+            meta[t[0]] = t[1:]
+    n, m = 2, 2
+    P = np.zeros((n, m, n), np.float32)
+    c = np.zeros(n * m, np.float32)
+    for (s, a), (cost, p) in rows.items():
+        P[s, a] = p
+        c[s * m + a] = cost
+    mdp = mdpgen.MDP(n=n, m=m, gamma=float(meta["gamma"][0]), fmt="dense", cost=c, P=P)
+    return mdp, meta
+
+
+def test_golden_two_state_closed_form():
+    mdp, meta = _golden_two_state()
+    jstar = np.array([float(x) for x in meta["jstar"]])
+    pistar = np.array([int(x) for x in meta["pistar"]])
+    pol = np.array([int(x) for x in meta["policy"][:2]])
+    val = np.array([float(x) for x in meta["policy"][3:5]])
+    for b in (1, 2):
+        r = oracle.mbvi(mdp, b, seed=7, eps=1e-14, max_sweeps=2000)
+        assert np.allclose(r["V"], jstar, rtol=0, atol=1e-12)
+        _, pi, _, _ = oracle.greedy(mdp, r["V"])
+        assert np.array_equal(pi, pistar)
+        ev = oracle.eval_policy(mdp, pol, b, seed=3, eps=1e-14, max_sweeps=5000)
+        assert np.allclose(ev["V"], val, rtol=0, atol=1e-10)
+    assert np.allclose(exact.policy_value(mdp, pol), val, atol=1e-12)
+    assert np.allclose(exact.brute_force(mdp), jstar, atol=1e-12)
+
+
+# ------------------------------------------------------------------------------------------------
+def _tiny_mdps():
+    out = []
+    for seed in range(3):
+        out.append(mdpgen.dense_dirichlet(6, 3, alpha=1.0, gamma=0.9, seed=seed))
+        out.append(mdpgen.csr_uniform_k(6, 3, 3, gamma=0.85, seed=10 + seed))
+    out.append(mdpgen.csr_ragged(5, 3, 4, gamma=0.8, seed=4, inadmissible_frac=0.3))
+    out.append(mdpgen.dense_dirichlet(5, 2, alpha=0.1, gamma=0.95, seed=9, cost_dist="normal"))
+    return out
+
+
+@pytest.mark.parametrize("idx", range(8))
+def test_mbvi_matches_brute_force(idx):
+    mdp = _tiny_mdps()[idx]
+    jstar = exact.brute_force(mdp)
+    # every optimal policy is greedy w.r.t. J*; brute force identifies J* uniquely
+    for b in sorted({1, 2, 3, mdp.n}):
+        for seed in (0, 1, 2):
+            r = oracle.mbvi(mdp, b, seed=seed, eps=1e-13, max_sweeps=20000)
+            assert np.max(np.abs(r["V"] - jstar)) < 1e-10, (b, seed)
+            TV, pi, gap, res = oracle.greedy(mdp, r["V"])
+            Jpi = exact.policy_value(mdp, pi)
+            sel = gap > 1e-9
+            assert np.max(np.abs(Jpi - jstar)[sel] if sel.any() else 0) < 1e-8
+
+
+@pytest.mark.parametrize("idx", range(8))
+def test_policy_evaluation_closed_form(idx):
+    mdp = _tiny_mdps()[idx]
+    c = mdp.cost.reshape(mdp.n, mdp.m)
+    rng = np.random.default_rng(idx)
+    pi = np.array([rng.choice(np.nonzero(np.isfinite(c[s]))[0]) for s in range(mdp.n)], np.int32)
+    J = exact.policy_value(mdp, pi)
+    for b in (1, 2, mdp.n):
+        r = oracle.eval_policy(mdp, pi, b, seed=5, eps=1e-13, max_sweeps=50000)
+        assert np.max(np.abs(r["V"] - J)) < 1e-10
+
+
+def test_policy_evaluation_closed_form_medium():
+    mdp = mdpgen.csr_uniform_k(3000, 4, 8, gamma=0.95, seed=3)
+    pi = mdpgen.random_policy(mdp.n, mdp.m, seed=1)
+    J = exact.policy_value(mdp, pi)
+    r = oracle.eval_policy(mdp, pi, 256, seed=12345, eps=1e-12, max_sweeps=5000)
+    assert np.max(np.abs(r["V"] - J)) < 1e-9
+
+
+# ------------------------------------------------------------------------------------------------
+def _definition_B(mdp, J, b, order, pi=None):
+    """B_b J evaluated literally from eqs. (10)-(12): state at 1-based position i of the processing
+    order reads BJ on M_b(i) = {first b*floor((i-1)/b) states of the order} and J elsewhere."""
+    n, m = mdp.n, mdp.m
+    BJ = {}
+    for i in range(1, n + 1):
+        s = int(order[i - 1])
+        M = set(int(x) for x in order[: b * ((i - 1) // b)])
+        acts = [int(pi[s])] if pi is not None else range(m)
+        vals = []
+        for a in acts:
+            r = s * m + a
+            g = float(mdp.cost[r])
+            if np.isinf(g):
+                vals.append(np.inf)
+                continue
+            if mdp.fmt == "dense":
+                succ = [(j, float(mdp.P[s, a, j])) for j in range(n)]
+            else:
+                succ = [(int(mdp.col[e]), float(mdp.prob[e])) for e in range(mdp.row_ptr[r], mdp.row_ptr[r + 1])]
+            tot = g
+            for j, p in succ:
+                tot += mdp.gamma * p * (BJ[j] if j in M else float(J[j]))
+            vals.append(tot)
+        BJ[s] = min(vals)
+    return np.array([BJ[s] for s in range(n)])
+
+
+@pytest.mark.parametrize("idx", range(8))
+def test_mb_apply_matches_set_definition(idx):
+    mdp = _tiny_mdps()[idx]
+    J = mdpgen.random_values(mdp.n, seed=idx).astype(np.float64)
+    pi = mdpgen.random_policy(mdp.n, mdp.m, seed=idx)
+    c = mdp.cost.reshape(mdp.n, mdp.m)
+    pi = np.where(np.isfinite(c[np.arange(mdp.n), pi]), pi, 0).astype(np.int32)
+    for b in range(1, mdp.n + 1):
+        for sweep in (0, 3):
+            order = oracle.perm(mdp.n, 12345, sweep)
+            got, _ = oracle.mb_apply(mdp, J, b, 12345, sweep)
+            assert np.allclose(got, _definition_B(mdp, J, b, order), rtol=0, atol=1e-12)
+            got, _ = oracle.mb_apply(mdp, J, b, 12345, sweep, pi=pi)
+            assert np.allclose(got, _definition_B(mdp, J, b, order, pi), rtol=0, atol=1e-12)
+
+
+def test_mb_apply_matches_set_definition_larger_ragged_tail():
+    mdp = mdpgen.csr_uniform_k(37, 3, 5, gamma=0.9, seed=2)
+    J = mdpgen.random_values(37, seed=1).astype(np.float64)
+    for b in (4, 5, 10, 36):
+        order = oracle.perm(37, 1, 9)
+        got, _ = oracle.mb_apply(mdp, J, b, 1, 9)
+        assert np.allclose(got, _definition_B(mdp, J, b, order), rtol=0, atol=1e-12)
+
+
+def test_reductions_b_equals_n_and_b_equals_1():
+    for mdp in (mdpgen.csr_uniform_k(300, 4, 8, gamma=0.9, seed=5), mdpgen.dense_dirichlet(120, 3, seed=6)):
+        J = mdpgen.random_values(mdp.n, seed=3).astype(np.float64)
+        got, _ = oracle.mb_apply(mdp, J, mdp.n, 77, 4)
+        assert np.array_equal(got, oracle.bellman_T(mdp, J))
+        assert np.allclose(got, exact.bellman_pass(mdp, J)[0], rtol=0, atol=1e-12)
+        got, _ = oracle.mb_apply(mdp, J, 1, 77, 4)
+        assert np.array_equal(got, oracle.gauss_seidel_F(mdp, oracle.perm(mdp.n, 77, 4), J))
+
+
+def test_delta_is_sup_norm_change():
+    mdp = mdpgen.csr_uniform_k(500, 4, 8, gamma=0.9, seed=8)
+    r = oracle.mbvi(mdp, 64, seed=3, eps=0, max_sweeps=6, traj=True)
+    prev = np.zeros(mdp.n)
+    for k in range(6):
+        assert r["deltas"][k] == np.max(np.abs(r["traj"][k] - prev))
+        prev = r["traj"][k]
+
+
+# ------------------------------------------------------------------------------------------------
+def _apply_k(mdp, J, b, k, seed=12345, pi=None):
+    V = np.array(J, dtype=np.float64)
+    for sweep in range(k):
+        V, _ = oracle.mb_apply(mdp, V, b, seed, sweep, pi=pi)
+    return V
+
+
+def test_shift_lemma_equality_fails_for_small_batches():
+    """For b < n the exact shift identity B(J + r e) = BJ + alpha r e is false (Sec. III-B.1
+    states it for every b); the states of earlier batches carry the shift alpha*r, not r."""
+    mdp = mdpgen.csr_uniform_k(200, 4, 6, gamma=0.9, seed=1)
+    J = mdpgen.random_values(200, seed=2).astype(np.float64)
+    BJ, _ = oracle.mb_apply(mdp, J, 7, 12345, 0)
+    Bs, _ = oracle.mb_apply(mdp, J + 1.0, 7, 12345, 0)
+    assert np.max(np.abs(Bs - BJ - mdp.gamma)) > 1e-3
+    # the first batch reads no updated state, so there the identity holds exactly
+    first = oracle.perm(200, 12345, 0)[:7]
+    assert np.max(np.abs((Bs - BJ - mdp.gamma)[first])) < 1e-7   # FP32 rows sum to 1 +- 4e-8
+
+
+@pytest.mark.parametrize("fmt", ["csr", "dense"])
+def test_monotonicity_shift_contraction(fmt):
+    # FP32 rows sum to 1 within ~4e-8, so shift / contraction bounds carry a 1e-7 slack
+    mdp = (mdpgen.csr_uniform_k(200, 4, 6, gamma=0.9, seed=1) if fmt == "csr"
+           else mdpgen.dense_dirichlet(80, 3, gamma=0.9, seed=2))
+    a = mdp.gamma
+    rng = np.random.default_rng(0)
+    pi = mdpgen.random_policy(mdp.n, mdp.m, seed=4)
+    for b in (1, 7, 32, mdp.n):
+        for trial in range(3):
+            J = rng.standard_normal(mdp.n)
+            Jp = J + np.abs(rng.standard_normal(mdp.n))          # J <= J'
+            for k in (1, 3):
+                for p in (None, pi):
+                    BJ, BJp = _apply_k(mdp, J, b, k, pi=p), _apply_k(mdp, Jp, b, k, pi=p)
+                    assert np.all(BJ <= BJp + 1e-12)                                   # monotonicity
+                    r = abs(float(rng.standard_normal()))
+                    Bs = _apply_k(mdp, J + r, b, k, pi=p)
+                    if b == mdp.n:                                                     # shift, b = n
+                        assert np.max(np.abs(Bs - (BJ + a ** k * r))) < 1e-7
+                    # b < n: the shift lemma's equality does not hold (its induction step shifts
+                    # the already-updated states by r instead of alpha*r); the sandwich does
+                    assert np.all(Bs >= BJ - 1e-12) and np.all(Bs <= BJ + a ** k * r + 1e-7)
+                    Bn = _apply_k(mdp, J - r, b, k, pi=p)
+                    assert np.all(Bn <= BJ + 1e-12) and np.all(Bn >= BJ - a ** k * r - 1e-7)
+                    Jq = rng.standard_normal(mdp.n)
+                    lhs = np.max(np.abs(BJ - _apply_k(mdp, Jq, b, k, pi=p)))
+                    assert lhs <= a ** k * np.max(np.abs(J - Jq)) + 1e-7               # contraction
+
+
+def test_fixed_point_and_error_bound():
+    mdp = mdpgen.csr_uniform_k(400, 5, 8, gamma=0.95, seed=11)
+    jstar, pistar, cert = exact.policy_iteration(mdp)
+    assert cert < 1e-12
+    for b in (1, 16, 400):
+        for sweep in (0, 5):
+            BJ, _ = oracle.mb_apply(mdp, jstar, b, 3, sweep)
+            assert np.max(np.abs(BJ - jstar)) < 1e-11
+            Bm, _ = oracle.mb_apply(mdp, exact.policy_value(mdp, pistar), b, 3, sweep, pi=pistar)
+            assert np.max(np.abs(Bm - jstar)) < 1e-11
+        # the FP32 rows sum to 1 only within ~4e-8: the sweep contracts by gamma * max row sum
+        g = mdp.gamma * float(np.add.reduceat(mdp.prob.astype(np.float64), mdp.row_ptr[:-1]).max())
+        for eps in (1e-3, 1e-6):
+            r = oracle.mbvi(mdp, b, seed=9, eps=eps, max_sweeps=10000)
+            d = r["deltas"][-1]
+            assert d <= eps
+            assert np.max(np.abs(r["V"] - jstar)) <= g / (1 - g) * d + 1e-12
+
+
+def test_comparison_theorem_divisor_chain():
+    """J=0 with costs >= 0 gives J <= TJ <= J*; then B_b^k J <= B_b'^k J <= J* for b' | b, and
+    T^k J <= B_b^k J <= F^k J (Sec. III-B.2), sweep by sweep with a shared permutation sequence."""
+    mdp = mdpgen.csr_uniform_k(256, 4, 6, gamma=0.95, seed=21)
+    jstar, _, _ = exact.policy_iteration(mdp)
+    J = np.zeros(mdp.n)
+    chain = [256, 64, 16, 4, 1]
+    V = {b: J.copy() for b in chain}
+    for sweep in range(25):
+        for b in chain:
+            V[b], _ = oracle.mb_apply(mdp, V[b], b, 4242, sweep)
+        for big, small in zip(chain[:-1], chain[1:]):
+            assert np.all(V[big] <= V[small] + 1e-12), (sweep, big, small)
+        assert np.all(V[1] <= jstar + 1e-12)
+    # the inequality is strict somewhere: smaller batches converge faster here
+    assert np.max(V[1] - V[256]) > 1e-3
+
+
+def test_mpi_matches_policy_iteration():
+    for mdp in (mdpgen.csr_uniform_k(300, 4, 8, gamma=0.95, seed=13), mdpgen.dense_dirichlet(60, 3, gamma=0.9, seed=1)):
+        jstar, pistar, _ = exact.policy_iteration(mdp)
+        for b in (1, 17, mdp.n):
+            r = oracle.mpi(mdp, b, K=10, seed=5, eps=1e-10, max_iters=10000)
+            assert r["resid"][-1] <= 1e-10
+            assert np.max(np.abs(r["V"] - jstar)) < 1e-8
+            _, _, gap, _ = exact.bellman_pass(mdp, jstar)
+            sel = gap > 1e-6
+            assert np.array_equal(r["pi"][sel], pistar[sel])
+            assert r["sweeps"] == 10 * (r["iters"] - 1)
+
+
+def test_inadmissible_actions_are_never_chosen():
+    mdp = mdpgen.csr_ragged(40, 4, 5, gamma=0.9, seed=3, inadmissible_frac=0.5)
+    r = oracle.mbvi(mdp, 8, seed=1, eps=1e-12, max_sweeps=10000)
+    _, pi, _, _ = oracle.greedy(mdp, r["V"])
+    assert np.all(np.isfinite(mdp.cost[np.arange(mdp.n) * mdp.m + pi]))
+    jstar, _, _ = exact.policy_iteration(mdp)
+    assert np.max(np.abs(r["V"] - jstar)) < 1e-9
+
+
+def test_mpi_first_outer_iteration_closed_form():
+    """Alg. 1 from J = 0: the improvement step picks mu0 = argmin_u g(i,u) (J = 0), then K sweeps
+    of B_{mu0,n} = T_mu0 give sum_{t<K} alpha^t P_mu0^t g_mu0 (eq. (6) iterated)."""
+    mdp = mdpgen.csr_uniform_k(150, 4, 6, gamma=0.9, seed=31)
+    c = mdp.cost.reshape(mdp.n, mdp.m).astype(np.float64)
+    mu0 = np.argmin(c, axis=1).astype(np.int32)
+    Pm, g = exact.policy_matrix(mdp, mu0)
+    K = 7
+    want, term = np.zeros(mdp.n), g.copy()
+    for t in range(K):
+        want += term
+        term = mdp.gamma * (Pm @ term)
+    r = oracle.mpi(mdp, mdp.n, K=K, seed=1, eps=0.0, max_iters=2)
+    assert r["iters"] == 2 and r["sweeps"] == K
+    assert np.max(np.abs(r["V"] - want)) < 1e-12
+    # with b < n the first sweep of B_{mu0,b} still starts from J = 0: the first batch equals g_mu0
+    r1 = oracle.mpi(mdp, 10, K=1, seed=1, eps=0.0, max_iters=2)
+    first = oracle.perm(mdp.n, 1, 0)[:10]
+    assert np.max(np.abs(r1["V"][first] - g[first])) < 1e-15
+
+
+def test_greedy_ties_resolve_to_lowest_action():
+    """Exact ties (duplicated actions) resolve to the lowest action index, with Q-gap 0."""
+    base = mdpgen.dense_dirichlet(30, 3, seed=5)
+    P = base.P.copy()
+    c = base.cost.reshape(30, 3).copy()
+    P[:, 2] = P[:, 1]
+    c[:, 2] = c[:, 1]          # action 2 duplicates action 1
+    P[:, 0] = P[:, 1]
+    c[:, 0] = c[:, 1] + 1.0    # action 0 is strictly worse
+    mdp = mdpgen.MDP(n=30, m=3, gamma=0.9, fmt="dense", cost=c.reshape(-1), P=P)
+    V = mdpgen.random_values(30, seed=1).astype(np.float64)
+    TV, pi, gap, _ = oracle.greedy(mdp, V)
+    assert np.all(pi == 1) and np.all(gap == 0)
+    r = oracle.mpi(mdp, 7, K=3, seed=2, eps=1e-10, max_iters=1000)
+    assert np.all(r["pi"] == 1)
