@@ -1,0 +1,189 @@
+/*
+ * rmb.h -- C ABI of librmb: the randomized mini-batch operator for finite discounted MDPs
+ * (Gargiani, Martinelli, Ruts Martinez, Lygeros, "Parallel and Flexible Dynamic Programming via
+ * the Randomized Mini-Batch Operator"), with value iteration, modified policy iteration and
+ * policy evaluation built on it, on one NVIDIA B300 (sm_103a).
+ *
+ * Problem (Sec. II-A): states S = {0..n-1}, m actions per state, transition rows P(.|s,a),
+ * stage costs g(s,a) (here "cost"), discount alpha (here "gamma") in (0,1).  An action outside
+ * U(s) carries cost +inf; every state needs at least one finite cost.
+ *
+ * Row r = s*m + a holds P(.|s,a).  Layouts (all arrays in device memory, caller-owned):
+ *   RMB_DENSE: P[n][m][n] float32, row-major (the m rows of a state are contiguous);
+ *   RMB_CSR:   row_ptr[n*m+1] int64 (row_ptr[0] = 0, non-decreasing), col[nnz] int32 in [0,n),
+ *              prob[nnz] float32 in [0,1];
+ *   both:      cost[n*m] float32.
+ * Rows should sum to 1 (checked to 1e-4 when opts.validate != 0).
+ *
+ * Values are float32 on the interface.  Inside a solve they are stored centred, V = mu + d, with
+ * mu a double and d float32; the reported residuals are exact differences of the stored values.
+ *
+ * Conventions shared by every entry point:
+ *   - Device pointers are caller-owned; the library never allocates device memory and never
+ *     frees anything.  Scratch memory ("workspace") is caller-provided, sized by
+ *     rmb_workspace_bytes, 256-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Every call is
+ *     asynchronous on that stream unless `stats` is non-NULL, in which case the call waits
+ *     for the stream and fills *stats (then the return value is the device-side status).
+ *   - Errors are returned as rmb_status codes; nothing aborts, exits or throws across the ABI.
+ *     Argument errors are reported before anything is launched.  Every grid-wide wait inside a
+ *     kernel gives up after opts.barrier_timeout_ns and reports RMB_ERR_BARRIER_TIMEOUT.
+ *   - On any error the outputs are unspecified.
+ */
+#ifndef RMB_H
+#define RMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RMB_OK = 0,
+    RMB_ERR_ARG = -1,              /* invalid argument (host check; nothing launched) */
+    RMB_ERR_CUDA = -2,             /* a CUDA runtime call or kernel launch failed */
+    RMB_ERR_NOT_CONVERGED = -3,    /* max_sweeps / max outer iterations reached above eps */
+    RMB_ERR_BARRIER_TIMEOUT = -4,  /* a grid-wide wait gave up; the kernel returned early */
+    RMB_ERR_INVALID_MDP = -5,      /* device validation: bad probability, index, row sum or cost */
+    RMB_ERR_WORKSPACE = -6,        /* workspace NULL, too small or not 256-byte aligned */
+    RMB_ERR_UNSUPPORTED = -7,      /* a size this build does not handle (n >= 2^31, ...) */
+    RMB_ERR_NONFINITE = -8         /* a value became NaN during the solve */
+} rmb_status;
+
+enum { RMB_DENSE = 0, RMB_CSR = 1 };
+
+/* The MDP (Sec. II-A).  All pointers are device pointers. */
+typedef struct {
+    int64_t n;               /* number of states, 1 <= n < 2^31 */
+    int32_t m;               /* actions per state, >= 1 */
+    int32_t format;          /* RMB_DENSE or RMB_CSR */
+    const float *P;          /* RMB_DENSE: [n*m*n] */
+    const int64_t *row_ptr;  /* RMB_CSR: [n*m+1] */
+    const int32_t *col;      /* RMB_CSR: [nnz] */
+    const float *prob;       /* RMB_CSR: [nnz] */
+    const float *cost;       /* [n*m]; +inf = action not admissible */
+    double gamma;            /* discount, 0 < gamma < 1 */
+    int32_t k_uniform;       /* RMB_CSR: k > 0 declares row_ptr[r] == r*k for every row (enables
+                                the vectorised row path; checked when validate != 0); 0 = unknown */
+    int32_t reserved;
+} rmb_mdp;
+
+/* Options of a solve. */
+typedef struct {
+    int64_t batch;           /* mini-batch size b (the paper's m), 1 <= b; b >= n means b = n */
+    uint64_t seed;           /* key of the per-sweep state permutation */
+    double eps;              /* stop when the residual <= eps (VI / evaluation: sup-norm change of a
+                                sweep; MPI: ||TV - V||_inf of the improvement pass) */
+    int64_t max_sweeps;      /* VI / evaluation: sweep limit; MPI: limit on improvement passes */
+    int64_t start_sweep;     /* index of the first sweep (the permutation of sweep k depends only on
+                                (seed, k), so a solve resumes exactly from V and start_sweep) */
+    int32_t eval_sweeps;     /* MPI: K evaluation sweeps per improvement (Alg. 1) */
+    int32_t validate;        /* != 0: run the device validation pass first */
+    int64_t barrier_timeout_ns; /* limit of every grid-wide wait; 0 = 2e9 (2 s) */
+    int32_t grid_ctas;       /* 0 = occupancy-sized persistent grid; else the number of CTAs */
+    int32_t flags;           /* RMB_FLAG_* */
+    double *trace;           /* optional device [max_sweeps] doubles: per-sweep residual (VI /
+                                evaluation) or per-improvement residual (MPI); NULL = none */
+} rmb_opts;
+
+/* Test-only fault injection: CTA 0 never arrives at the first grid-wide wait, so every wait runs
+   out and the call must report RMB_ERR_BARRIER_TIMEOUT with the GPU context intact. */
+#define RMB_FLAG_INJECT_BARRIER_STALL 1
+
+/* Results of a solve (filled only when a stats pointer is passed). */
+typedef struct {
+    int64_t sweeps;          /* applications of B_b / B_{pi,b} done */
+    int64_t iters;           /* MPI: improvement passes done; else 0 */
+    int64_t barriers;        /* grid-wide waits crossed */
+    double residual;         /* last residual (see rmb_opts.eps) */
+    double v_shift;          /* centring offset mu at exit */
+    int32_t status;          /* device-side rmb_status */
+    int32_t grid_ctas;       /* CTAs of the persistent launch */
+    int32_t path;            /* 0 dense, 1 CSR vectorised rows, 2 CSR generic rows */
+    int32_t lanes_per_state; /* CSR paths: lanes that share one state */
+    float ms;                /* device time of the call (CUDA events on `stream`) */
+    int32_t reserved;
+} rmb_stats;
+
+/* Bytes of workspace a call with this MDP and these options needs (0 on invalid arguments). */
+size_t rmb_workspace_bytes(const rmb_mdp *mdp, const rmb_opts *opts);
+
+/*
+ * MB-VI (Sec. III-B: B_b of eq. (11) in place of T in value iteration).
+ * Sweep k = start_sweep, start_sweep+1, ... re-indexes the states by a Philox-keyed permutation
+ * sigma_{seed,k} (Sec. III-A, Sec. IV-A) and updates them in batches of b positions: every
+ * state of batch t reads the new values of batches < t and the old values of the rest (its own
+ * batch included), so b = 1 is Gauss-Seidel and b = n is the Bellman operator T.
+ * Stops after the first sweep whose sup-norm change is <= eps, or after max_sweeps sweeps.
+ *   V_inout  [n] float32: start values on entry (the paper uses 0), final values on exit.
+ *   pi_out   [n] int32 or NULL: greedy policy at the final values (lowest action on ties).
+ *   qgap_out [n] float32 or NULL: second smallest minus smallest Q-factor at the final values.
+ */
+int rmb_vi(const rmb_mdp *mdp, const rmb_opts *opts, float *V_inout, int32_t *pi_out,
+           float *qgap_out, void *workspace, size_t workspace_bytes, rmb_stats *stats,
+           void *stream);
+
+/*
+ * MB-MPI (Alg. 1 with B_{pi,b} of eq. (12) in the evaluation step, Sec. III-B), warm-started:
+ * repeat { improvement pass: pi = greedy(V), r = ||TV - V||_inf (V unchanged); stop if r <= eps
+ * or after max_sweeps passes; K = eval_sweeps sweeps V <- B_{pi,b} V }.  The permutation's
+ * sweep counter runs on across all evaluation sweeps.
+ *   V_inout [n]: start values / final values.  pi_out [n] (required): the final greedy policy.
+ *   qgap_out [n] or NULL: Q-gap of the final improvement pass.
+ */
+int rmb_mpi(const rmb_mdp *mdp, const rmb_opts *opts, float *V_inout, int32_t *pi_out,
+            float *qgap_out, void *workspace, size_t workspace_bytes, rmb_stats *stats,
+            void *stream);
+
+/*
+ * Mini-batch policy evaluation: sweeps V <- B_{pi,b} V (eq. (12)) until the sup-norm change of a
+ * sweep is <= eps or max_sweeps sweeps are done.  Converges to J_pi of eq. (4).
+ *   pi [n] int32 in [0,m), admissible actions only.  V_inout [n]: start / final values.
+ */
+int rmb_eval_policy(const rmb_mdp *mdp, const int32_t *pi, const rmb_opts *opts, float *V_inout,
+                    void *workspace, size_t workspace_bytes, rmb_stats *stats, void *stream);
+
+/*
+ * One full Bellman pass at V (eq. (7)) and the improvement step of Alg. 1:
+ *   TV_out [n] or NULL, pi_out [n] or NULL (lowest action on ties), qgap_out [n] or NULL.
+ * stats->residual = ||TV - V||_inf.  Only opts.validate, grid_ctas, barrier_timeout_ns and flags
+ * are used.
+ */
+int rmb_greedy(const rmb_mdp *mdp, const rmb_opts *opts, const float *V, float *TV_out,
+               int32_t *pi_out, float *qgap_out, void *workspace, size_t workspace_bytes,
+               rmb_stats *stats, void *stream);
+
+/*
+ * The processing order of sweep k (Sec. III-A): out[p] = sigma_{seed,k}(p), p = 0..n-1, a
+ * bijection of [0,n).  An 8-round balanced Feistel network on 2h-bit words with
+ * h = max(1, ceil(ceil(log2 n)/2)) and round function Philox4x32-10(ctr = {R, round, k_lo, k_hi},
+ * key = {seed_lo, seed_hi}).x0 mod 2^h (Salmon et al., SC'11), cycle-walked into [0,n).
+ *   out [n] int32, device.
+ */
+int rmb_permutation(int64_t n, uint64_t seed, uint64_t sweep, int32_t *out, void *stream);
+
+/*
+ * Device validation of an MDP: probabilities finite and in [0,1], |row sum - 1| <= 1e-4,
+ * indices in [0,n), row_ptr non-decreasing from 0 (and == r*k when k_uniform is declared),
+ * costs not NaN and not -inf, at least one admissible action per state.
+ * Synchronous: returns RMB_OK or RMB_ERR_INVALID_MDP (or an argument / CUDA error).
+ *   workspace: at least 256 bytes (its first 256 bytes are used).
+ */
+int rmb_validate(const rmb_mdp *mdp, void *workspace, size_t workspace_bytes, void *stream);
+
+/* Static text for a status code. */
+const char *rmb_status_string(int status);
+
+/* Number of kernels this library has launched in this process (all devices, all threads). */
+uint64_t rmb_kernel_launches(void);
+
+/* ABI version: (major << 16) | minor. */
+int rmb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RMB_H */

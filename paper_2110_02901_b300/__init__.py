@@ -1,0 +1,320 @@
+"""Python binding of librmb (include/rmb.h): the randomized mini-batch operator on a B300.
+
+Thin ctypes marshalling only: every step of a solve runs in the CUDA kernels of ``librmb.so``.
+PyTorch supplies device memory and streams.  The C entry points keep their names here
+(``rmb_vi``, ``rmb_mpi``, ``rmb_eval_policy``, ``rmb_greedy``, ``rmb_permutation``,
+``rmb_validate``, ``rmb_workspace_bytes``, ``rmb_status_string``); they take torch CUDA tensors.
+
+There is no CPU fallback: if ``librmb.so`` is missing or cannot be loaded, importing the library
+handle raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librmb.so")
+
+RMB_OK = 0
+RMB_ERR_ARG = -1
+RMB_ERR_CUDA = -2
+RMB_ERR_NOT_CONVERGED = -3
+RMB_ERR_BARRIER_TIMEOUT = -4
+RMB_ERR_INVALID_MDP = -5
+RMB_ERR_WORKSPACE = -6
+RMB_ERR_UNSUPPORTED = -7
+RMB_ERR_NONFINITE = -8
+RMB_DENSE = 0
+RMB_CSR = 1
+RMB_FLAG_INJECT_BARRIER_STALL = 1
+PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic"}
+
+
+class rmb_mdp(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64), ("m", ctypes.c_int32), ("format", ctypes.c_int32),
+        ("P", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
+        ("prob", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("gamma", ctypes.c_double),
+        ("k_uniform", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+class rmb_opts(ctypes.Structure):
+    _fields_ = [
+        ("batch", ctypes.c_int64), ("seed", ctypes.c_uint64), ("eps", ctypes.c_double),
+        ("max_sweeps", ctypes.c_int64), ("start_sweep", ctypes.c_int64),
+        ("eval_sweeps", ctypes.c_int32), ("validate", ctypes.c_int32),
+        ("barrier_timeout_ns", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
+        ("flags", ctypes.c_int32), ("trace", ctypes.c_void_p),
+    ]
+
+
+class rmb_stats(ctypes.Structure):
+    _fields_ = [
+        ("sweeps", ctypes.c_int64), ("iters", ctypes.c_int64), ("barriers", ctypes.c_int64),
+        ("residual", ctypes.c_double), ("v_shift", ctypes.c_double), ("status", ctypes.c_int32),
+        ("grid_ctas", ctypes.c_int32), ("path", ctypes.c_int32), ("lanes_per_state", ctypes.c_int32),
+        ("ms", ctypes.c_float), ("reserved", ctypes.c_int32),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d["path"] = PATH_NAMES.get(d["path"], d["path"])
+        d["status_text"] = rmb_status_string(d["status"])
+        return d
+
+
+_LIB = None
+
+
+def lib():
+    """The loaded librmb.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"librmb.so not built at {LIB_PATH} (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        P, vp, sz = ctypes.POINTER, ctypes.c_void_p, ctypes.c_size_t
+        L.rmb_workspace_bytes.argtypes = [P(rmb_mdp), P(rmb_opts)]
+        L.rmb_workspace_bytes.restype = sz
+        L.rmb_vi.argtypes = [P(rmb_mdp), P(rmb_opts), vp, vp, vp, vp, sz, P(rmb_stats), vp]
+        L.rmb_mpi.argtypes = [P(rmb_mdp), P(rmb_opts), vp, vp, vp, vp, sz, P(rmb_stats), vp]
+        L.rmb_eval_policy.argtypes = [P(rmb_mdp), vp, P(rmb_opts), vp, vp, sz, P(rmb_stats), vp]
+        L.rmb_greedy.argtypes = [P(rmb_mdp), P(rmb_opts), vp, vp, vp, vp, vp, sz, P(rmb_stats), vp]
+        L.rmb_permutation.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, vp, vp]
+        L.rmb_validate.argtypes = [P(rmb_mdp), vp, sz, vp]
+        L.rmb_status_string.argtypes = [ctypes.c_int]
+        L.rmb_status_string.restype = ctypes.c_char_p
+        L.rmb_kernel_launches.restype = ctypes.c_uint64
+        L.rmb_version.restype = ctypes.c_int
+        for f in ("rmb_vi", "rmb_mpi", "rmb_eval_policy", "rmb_greedy", "rmb_permutation", "rmb_validate"):
+            getattr(L, f).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+class RmbError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {rmb_status_string(status)} ({status})")
+
+
+def rmb_status_string(status: int) -> str:
+    return lib().rmb_status_string(int(status)).decode()
+
+
+def rmb_kernel_launches() -> int:
+    return int(lib().rmb_kernel_launches())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return int(t.data_ptr())
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) or None
+
+
+def _check(t, dtype, n, name):
+    import torch
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() < n:
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor with >= {n} elements")
+
+
+# ----------------------------------------------------------------------------------------------
+class DeviceMDP:
+    """An MDP resident in device memory (torch tensors) plus its rmb_mdp descriptor."""
+
+    def __init__(self, n, m, gamma, fmt, cost, P=None, row_ptr=None, col=None, prob=None,
+                 k_uniform: int = 0, name: str = ""):
+        self.n, self.m, self.gamma, self.fmt, self.name = int(n), int(m), float(gamma), fmt, name
+        self.cost, self.P, self.row_ptr, self.col, self.prob = cost, P, row_ptr, col, prob
+        self.k_uniform = int(k_uniform)
+        d = rmb_mdp()
+        d.n, d.m, d.gamma = self.n, self.m, self.gamma
+        d.format = RMB_DENSE if fmt == "dense" else RMB_CSR
+        d.cost = _ptr(cost)
+        d.P, d.row_ptr, d.col, d.prob = _ptr(P), _ptr(row_ptr), _ptr(col), _ptr(prob)
+        d.k_uniform = self.k_uniform
+        self.desc = d
+
+    @classmethod
+    def from_host(cls, mdp, device="cuda", non_blocking=False):
+        """Upload an ``mdpgen.MDP`` (numpy arrays) to the device."""
+        import torch
+
+        def up(a):
+            if a is None:
+                return None
+            return torch.from_numpy(np.ascontiguousarray(a)).to(device, non_blocking=non_blocking)
+
+        return cls(mdp.n, mdp.m, mdp.gamma, mdp.fmt, up(mdp.cost), P=up(mdp.P), row_ptr=up(mdp.row_ptr),
+                   col=up(mdp.col), prob=up(mdp.prob),
+                   k_uniform=mdp.uniform_k() if mdp.fmt == "csr" else 0, name=getattr(mdp, "name", ""))
+
+    @property
+    def nnz(self) -> int:
+        return self.n * self.m * self.n if self.fmt == "dense" else int(self.prob.numel())
+
+
+@dataclasses.dataclass
+class Opts:
+    batch: int
+    seed: int = 12345
+    eps: float = 1e-6
+    max_sweeps: int = 100000
+    start_sweep: int = 0
+    eval_sweeps: int = 10
+    validate: bool = True
+    barrier_timeout_ns: int = 0
+    grid_ctas: int = 0
+    flags: int = 0
+    trace: object = None       # optional torch float64 CUDA tensor [max_sweeps]
+
+    def desc(self) -> rmb_opts:
+        o = rmb_opts()
+        o.batch, o.seed, o.eps = int(self.batch), int(self.seed) & (2 ** 64 - 1), float(self.eps)
+        o.max_sweeps, o.start_sweep = int(self.max_sweeps), int(self.start_sweep)
+        o.eval_sweeps, o.validate = int(self.eval_sweeps), int(bool(self.validate))
+        o.barrier_timeout_ns, o.grid_ctas, o.flags = int(self.barrier_timeout_ns), int(self.grid_ctas), int(self.flags)
+        o.trace = _ptr(self.trace)
+        return o
+
+
+def rmb_workspace_bytes(mdp: DeviceMDP, opts: Opts) -> int:
+    o = opts.desc()
+    return int(lib().rmb_workspace_bytes(ctypes.byref(mdp.desc), ctypes.byref(o)))
+
+
+def workspace(mdp: DeviceMDP, opts: Opts, device="cuda"):
+    import torch
+    nb = rmb_workspace_bytes(mdp, opts)
+    if nb == 0:
+        raise RmbError(RMB_ERR_ARG, "rmb_workspace_bytes")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def _finish(st: int, stats: Optional[rmb_stats], what: str, allow=(RMB_OK, RMB_ERR_NOT_CONVERGED)):
+    if st not in allow:
+        raise RmbError(st, what)
+    return stats.as_dict() if stats is not None else None
+
+
+def rmb_vi(mdp: DeviceMDP, opts: Opts, V, pi=None, qgap=None, ws=None, stats: bool = True, stream=None,
+           check: bool = True):
+    """MB-VI in place on V (float32 [n]); returns the stats dict (or None when stats=False)."""
+    import torch
+    _check(V, torch.float32, mdp.n, "V")
+    _check(pi, torch.int32, mdp.n, "pi")
+    _check(qgap, torch.float32, mdp.n, "qgap")
+    ws = workspace(mdp, opts) if ws is None else ws
+    o = opts.desc()
+    s = rmb_stats() if stats else None
+    st = lib().rmb_vi(ctypes.byref(mdp.desc), ctypes.byref(o), _ptr(V), _ptr(pi), _ptr(qgap), _ptr(ws),
+                      ws.numel(), ctypes.byref(s) if s is not None else None, _stream_handle(stream))
+    return _finish(st, s, "rmb_vi") if check else (st, s.as_dict() if s is not None else None)
+
+
+def rmb_mpi(mdp: DeviceMDP, opts: Opts, V, pi, qgap=None, ws=None, stats: bool = True, stream=None,
+            check: bool = True):
+    """MB-MPI in place on V; pi (int32 [n]) receives the final greedy policy."""
+    import torch
+    _check(V, torch.float32, mdp.n, "V")
+    _check(pi, torch.int32, mdp.n, "pi")
+    _check(qgap, torch.float32, mdp.n, "qgap")
+    ws = workspace(mdp, opts) if ws is None else ws
+    o = opts.desc()
+    s = rmb_stats() if stats else None
+    st = lib().rmb_mpi(ctypes.byref(mdp.desc), ctypes.byref(o), _ptr(V), _ptr(pi), _ptr(qgap), _ptr(ws),
+                       ws.numel(), ctypes.byref(s) if s is not None else None, _stream_handle(stream))
+    return _finish(st, s, "rmb_mpi") if check else (st, s.as_dict() if s is not None else None)
+
+
+def rmb_eval_policy(mdp: DeviceMDP, pi, opts: Opts, V, ws=None, stats: bool = True, stream=None,
+                    check: bool = True):
+    """Mini-batch policy evaluation (B_{pi,b} sweeps) in place on V."""
+    import torch
+    _check(V, torch.float32, mdp.n, "V")
+    _check(pi, torch.int32, mdp.n, "pi")
+    ws = workspace(mdp, opts) if ws is None else ws
+    o = opts.desc()
+    s = rmb_stats() if stats else None
+    st = lib().rmb_eval_policy(ctypes.byref(mdp.desc), _ptr(pi), ctypes.byref(o), _ptr(V), _ptr(ws), ws.numel(),
+                               ctypes.byref(s) if s is not None else None, _stream_handle(stream))
+    return _finish(st, s, "rmb_eval_policy") if check else (st, s.as_dict() if s is not None else None)
+
+
+def rmb_greedy(mdp: DeviceMDP, V, TV=None, pi=None, qgap=None, opts: Optional[Opts] = None, ws=None,
+               stats: bool = True, stream=None, check: bool = True):
+    """One Bellman pass at V: TV, greedy policy, Q-gap; stats['residual'] = ||TV - V||_inf."""
+    import torch
+    opts = opts or Opts(batch=mdp.n)
+    _check(V, torch.float32, mdp.n, "V")
+    _check(TV, torch.float32, mdp.n, "TV")
+    _check(pi, torch.int32, mdp.n, "pi")
+    _check(qgap, torch.float32, mdp.n, "qgap")
+    ws = workspace(mdp, opts) if ws is None else ws
+    o = opts.desc()
+    s = rmb_stats() if stats else None
+    st = lib().rmb_greedy(ctypes.byref(mdp.desc), ctypes.byref(o), _ptr(V), _ptr(TV), _ptr(pi), _ptr(qgap),
+                          _ptr(ws), ws.numel(), ctypes.byref(s) if s is not None else None, _stream_handle(stream))
+    return _finish(st, s, "rmb_greedy", allow=(RMB_OK,)) if check else (st, s.as_dict() if s is not None else None)
+
+
+def rmb_permutation(n: int, seed: int, sweep: int, out=None, stream=None):
+    """sigma_{seed,sweep}(p) for p = 0..n-1 as an int32 CUDA tensor."""
+    import torch
+    out = torch.empty(int(n), dtype=torch.int32, device="cuda") if out is None else out
+    _check(out, torch.int32, n, "out")
+    st = lib().rmb_permutation(int(n), int(seed) & (2 ** 64 - 1), int(sweep) & (2 ** 64 - 1), _ptr(out),
+                               _stream_handle(stream))
+    if st != RMB_OK:
+        raise RmbError(st, "rmb_permutation")
+    return out
+
+
+def rmb_validate(mdp: DeviceMDP, ws=None, stream=None) -> int:
+    """Synchronous device validation; returns RMB_OK or RMB_ERR_INVALID_MDP."""
+    import torch
+    ws = torch.empty(256, dtype=torch.uint8, device="cuda") if ws is None else ws
+    return int(lib().rmb_validate(ctypes.byref(mdp.desc), _ptr(ws), ws.numel(), _stream_handle(stream)))
+
+
+# ----------------------------------------------------------------------------------------------
+# Convenience: allocate outputs with torch and run a solve.
+# ----------------------------------------------------------------------------------------------
+def vi(mdp: DeviceMDP, opts: Opts, V0=None, want_policy: bool = True):
+    import torch
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda") if V0 is None else V0.clone()
+    pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda") if want_policy else None
+    gap = torch.empty(mdp.n, dtype=torch.float32, device="cuda") if want_policy else None
+    st = rmb_vi(mdp, opts, V, pi, gap)
+    return {"V": V, "pi": pi, "qgap": gap, "stats": st}
+
+
+def mpi(mdp: DeviceMDP, opts: Opts, V0=None):
+    import torch
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda") if V0 is None else V0.clone()
+    pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
+    gap = torch.empty(mdp.n, dtype=torch.float32, device="cuda")
+    st = rmb_mpi(mdp, opts, V, pi, gap)
+    return {"V": V, "pi": pi, "qgap": gap, "stats": st}
+
+
+def eval_policy(mdp: DeviceMDP, pi, opts: Opts, V0=None):
+    import torch
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda") if V0 is None else V0.clone()
+    st = rmb_eval_policy(mdp, pi, opts, V)
+    return {"V": V, "stats": st}

@@ -1,0 +1,1219 @@
+// librmb: the randomized mini-batch operator (Gargiani et al., Sec. III) and the VI / MPI /
+// policy-evaluation schemes built on it, as persistent sm_103a kernels behind the C ABI of rmb.h.
+//
+// One launch runs a whole solve.  Every CTA walks the same sequence of phases and all control
+// decisions (stop, re-centre) are taken from values every CTA reads after the same grid-wide wait,
+// so the grid stays in step without host round trips.
+//
+// Mini-batch semantics (eq. (11)): within sweep k, positions [t*b, (t+1)*b) of the order
+// sigma_{seed,k} form batch t; a state of batch t must read the new values of batches < t and the
+// old values of every other state, its own batch included.  Two value buffers make that hold with
+// one grid-wide wait per batch: batch t reads buffer A_t = d[(c+t)&1] and writes its new values
+// into B_t = d[(c+t+1)&1], together with the new values of batch t-1 (kept in a small position-
+// indexed cache), so that before batch t the buffer A_t holds exactly "batches < t new, rest old".
+// At the end of a sweep with two or more batches the last batch is copied once more, so both
+// buffers agree when the next sweep (with a new permutation) starts.
+//
+// Values are stored centred: V = mu + d with mu a double shared by the grid and d float32, so the
+// float32 arithmetic works on differences of size ~ the spread of V instead of |V|.  With rows
+// summing to 1, V'(s) = min_a [c + gamma sum p (mu + d)] gives d'(s) = min_a [c + gamma sum p d]
+// - (1 - gamma) mu.  mu moves (and every d with it) only between sweeps, when the midpoint of the
+// values drifts by more than a quarter of their spread.
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+
+#include "rmb.h"
+#include "rmb_device.cuh"
+
+namespace rmb {
+
+enum Mode { MODE_VI = 0, MODE_EVAL = 1, MODE_MPI = 2, MODE_GREEDY = 3 };
+enum Path { PATH_DENSE = 0, PATH_CSR_VEC = 1, PATH_CSR_GEN = 2 };
+enum Kind { K_MIN = 0, K_POLICY = 1, K_GREEDY = 2 };
+
+constexpr int kCsrThreads = 512;
+constexpr int kDenseThreads = 256;
+constexpr int kDenseMaxM = 256;
+constexpr int kDenseMB = 8;               // actions accumulated per pass in the dense path
+constexpr int kDenseMaxStage = 40960;     // floats of V staged at once (160 KB of shared memory)
+
+struct KP {
+    // problem
+    int n, m, k, path;
+    const float* P;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* prob;
+    const float* cost;
+    float gamma;
+    double gamma_d;
+    // schedule
+    int mode, b, T, last_len, K;
+    long long start_sweep, max_sweeps;
+    double eps;
+    uint32_t seed_lo, seed_hi, h;
+    int lps_all, lps_one;   // CSR: lanes sharing one state (all actions / one row)
+    int stage;              // dense: floats of V staged per chunk
+    // buffers
+    const float* Vin;
+    float* Vout;
+    float* TVout;
+    int32_t* pi;            // VI / MPI / greedy: policy output (MPI: also the evaluated policy)
+    float* qgap;
+    const int32_t* pi_in;   // evaluation: the policy
+    float* d[2];
+    int32_t* S[2];
+    float* W[2];
+    Ctrl* ctrl;
+    double* trace;
+    long long timeout_ns;
+    int flags;
+};
+
+struct Best {
+    float q;
+    int a;
+    float q2;
+};
+
+__device__ __forceinline__ Best better(const Best& x, const Best& y)
+{
+    const bool xf = (x.q < y.q) || (x.q == y.q && x.a < y.a);
+    Best w = xf ? x : y;
+    const float lq = xf ? y.q : x.q;
+    w.q2 = fminf(w.q2, lq);
+    return w;
+}
+
+template <bool ARG>
+__device__ __forceinline__ Best shfl_xor_best(Best v, int off)
+{
+    Best o;
+    o.q = __shfl_xor_sync(0xffffffffu, v.q, off);
+    if (ARG) {
+        o.a = __shfl_xor_sync(0xffffffffu, v.a, off);
+        o.q2 = __shfl_xor_sync(0xffffffffu, v.q2, off);
+    } else {
+        o.a = 0;
+        o.q2 = kInf;
+    }
+    return o;
+}
+
+__device__ __forceinline__ float gather(const float* __restrict__ A, int j, uint32_t nm1)
+{
+    // clamp keeps an unvalidated bad index inside the buffer (validation reports it)
+    return ld_l2(A + min((uint32_t)j, nm1));
+}
+
+// Q-factors of one state on the vectorised CSR path (every row has k entries, k % 4 == 0).
+// `lps` lanes share the state: cpr lanes per row, each reading whole float4/int4 chunks; rows
+// are combined with xor-shuffles.  Inactive groups still take part in the shuffles.
+template <bool ARG>
+__device__ __forceinline__ Best csr_vec_state(const KP& p, int s, int pi_s, bool act,
+                                              const float* __restrict__ A, int lps, int lane_g)
+{
+    const int k4 = p.k >> 2;
+    const int cpr = k4 < lps ? k4 : lps;
+    const int cpl = k4 / cpr;
+    const int rpi = lps / cpr;
+    const int slot = lane_g / cpr, ch = lane_g - slot * cpr;
+    const int nrows = pi_s >= 0 ? 1 : p.m;
+    const uint32_t nm1 = (uint32_t)(p.n - 1);
+    Best best = {kInf, 0x7fffffff, kInf};
+    for (int a0 = 0; a0 < nrows; a0 += rpi) {
+        const int ai = a0 + slot;
+        const bool valid = act && ai < nrows;
+        const int a = pi_s >= 0 ? pi_s : ai;
+        const int64_t r = (int64_t)s * p.m + a;
+        float part = 0.f;
+        if (valid) {
+            const float4* pr = reinterpret_cast<const float4*>(p.prob + r * p.k) + ch;
+            const int4* cr = reinterpret_cast<const int4*>(p.col + r * p.k) + ch;
+            for (int c = 0; c < cpl; ++c) {
+                const float4 pv = __ldcs(pr + c * cpr);
+                const int4 cv = __ldcs(cr + c * cpr);
+                part = fmaf(pv.x, gather(A, cv.x, nm1), part);
+                part = fmaf(pv.y, gather(A, cv.y, nm1), part);
+                part = fmaf(pv.z, gather(A, cv.z, nm1), part);
+                part = fmaf(pv.w, gather(A, cv.w, nm1), part);
+            }
+        }
+        for (int off = 1; off < cpr; off <<= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        Best cur = {kInf, valid ? a : 0x7fffffff, kInf};
+        if (valid) {
+            const float c = __ldg(p.cost + r);
+            cur.q = (c == kInf) ? kInf : fmaf(p.gamma, part, c);
+        }
+        for (int off = cpr; off < lps; off <<= 1) cur = better(cur, shfl_xor_best<ARG>(cur, off));
+        best = better(best, cur);
+    }
+    return best;
+}
+
+// Q-factors of one state on the generic CSR path (ragged rows): the whole warp walks each row.
+template <bool ARG>
+__device__ __forceinline__ Best csr_gen_state(const KP& p, int s, int pi_s, bool act,
+                                              const float* __restrict__ A, int lane)
+{
+    const int nrows = pi_s >= 0 ? 1 : p.m;
+    const uint32_t nm1 = (uint32_t)(p.n - 1);
+    Best best = {kInf, 0x7fffffff, kInf};
+    for (int ai = 0; ai < nrows; ++ai) {
+        const int a = pi_s >= 0 ? pi_s : ai;
+        const int64_t r = (int64_t)s * p.m + a;
+        float part = 0.f;
+        int64_t e0 = 0, e1 = 0;
+        if (act) {
+            e0 = __ldg(p.row_ptr + r);
+            e1 = __ldg(p.row_ptr + r + 1);
+        }
+        for (int64_t e = e0 + lane; e < e1; e += 32)
+            part = fmaf(__ldcs(p.prob + e), gather(A, __ldcs(p.col + e), nm1), part);
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        Best cur = {kInf, act ? a : 0x7fffffff, kInf};
+        if (act) {
+            const float c = __ldg(p.cost + r);
+            cur.q = (c == kInf) ? kInf : fmaf(p.gamma, part, c);
+        }
+        best = better(best, cur);
+    }
+    return best;
+}
+
+struct Acc {
+    float dmax, vlo, vhi;
+};
+
+struct Centre {
+    double mu;
+    float kap_hi, kap_lo;   // (1 - gamma) mu split in two floats
+    float gmu;              // gamma * mu (float; only for TV output)
+};
+
+__device__ __forceinline__ Centre make_centre(double mu, double gamma)
+{
+    Centre c;
+    c.mu = mu;
+    const double kap = (1.0 - gamma) * mu;
+    c.kap_hi = (float)kap;
+    c.kap_lo = (float)(kap - (double)c.kap_hi);
+    c.gmu = (float)(gamma * mu);
+    return c;
+}
+
+__device__ __forceinline__ float new_value(float q, const Centre& C) { return (q - C.kap_hi) - C.kap_lo; }
+
+// Per-state epilogue shared by the CSR and dense paths.
+template <int KIND>
+__device__ __forceinline__ void state_epilogue(const KP& p, const Best& r, int s, int i, const float* A,
+                                               float* B, int32_t* Sout, float* Wout, const Centre& C,
+                                               Acc& acc)
+{
+    const float old = ld_l2(A + s);
+    const float v = new_value(r.q, C);
+    if (v != v) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
+    if (KIND == K_GREEDY) {
+        acc.dmax = fmaxf(acc.dmax, fabsf(v - old));          // ||TV - V||_inf
+        if (p.pi) st_l2(p.pi + s, r.a);
+        if (p.qgap) p.qgap[s] = r.q2 - r.q;
+        if (p.TVout) p.TVout[s] = (float)((double)r.q + p.gamma_d * C.mu);
+        if (p.Vout) p.Vout[s] = (float)(C.mu + (double)old);
+    } else {
+        acc.dmax = fmaxf(acc.dmax, fabsf(v - old));
+        acc.vlo = fminf(acc.vlo, v);
+        acc.vhi = fmaxf(acc.vhi, v);
+        st_l2(Sout + i, s);
+        st_l2(Wout + i, v);
+        st_l2(B + s, v);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// One batch (or, for K_GREEDY, the full state set in natural order) on the CSR paths.
+// Unit = a group of lps lanes; position i of the batch goes to unit (i mod U), step (i div U).
+// ------------------------------------------------------------------------------------------------
+template <int KIND, bool VEC>
+__device__ void csr_batch(const KP& p, int lps, const float* __restrict__ A, float* B, int pos0, int len,
+                          const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc,
+                          bool* perm_ok)
+{
+    constexpr bool ARG = (KIND == K_GREEDY);
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int spw = 32 / lps;
+    const int g = lane / lps, lane_g = lane - g * lps;
+    const int U = nwarps * spw;
+    const int first = warp * spw;
+    for (int j0 = 0; first + j0 * U < len; j0 += 32 / spw) {
+        // each lane resolves the state of one (group, step) pair of the next 32/spw steps
+        const int my_pos = first + (lane % spw) + (j0 + lane / spw) * U;
+        int my_state = -1;
+        if (my_pos < len) my_state = K ? (int)perm_at((uint32_t)(pos0 + my_pos), *K, perm_ok) : pos0 + my_pos;
+        for (int jj = 0; jj < 32 / spw; ++jj) {
+            const int j = j0 + jj;
+            if (first + j * U >= len) break;
+            const int s = __shfl_sync(0xffffffffu, my_state, jj * spw + g);
+            const bool act = s >= 0;
+            const int ss = act ? s : 0;
+            const int pi_s = (KIND == K_POLICY)
+                                 ? (act ? (int)min((uint32_t)ld_l2(p.pi_in ? p.pi_in + ss : p.pi + ss), (uint32_t)(p.m - 1)) : 0)
+                                 : -1;
+            const Best r = VEC ? csr_vec_state<ARG>(p, ss, pi_s, act, A, lps, lane_g)
+                               : csr_gen_state<ARG>(p, ss, pi_s, act, A, lane);
+            if (act && lane_g == 0) state_epilogue<KIND>(p, r, s, first + g + j * U, A, B, Sout, Wout, C, acc);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Dense path: one CTA per state, the current values staged in shared memory by a bulk async copy.
+// ------------------------------------------------------------------------------------------------
+struct DenseSmem {
+    uint64_t mbar;
+    uint32_t phase;
+    int ok;
+    float red[kDenseThreads / 32][kDenseMB];
+    float q[kDenseMaxM];
+    int perm[32];
+};
+
+__device__ __forceinline__ int try_wait_bounded(uint32_t mb, uint32_t parity, long long timeout_ns)
+{
+    uint32_t done = 0, spins = 0;
+    const uint64_t t0 = globaltimer_ns();
+    while (!done) {
+        asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                     : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+        if (!done && (++spins & 63u) == 0 && (int64_t)(globaltimer_ns() - t0) > timeout_ns) return 0;
+    }
+    return 1;
+}
+
+__device__ __forceinline__ bool stage_values(const KP& p, DenseSmem& sm, float* dst, const float* src, int nfl)
+{
+    // nfl is a multiple of 4 floats (16 bytes), src and dst 16-byte aligned
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&sm.mbar);
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const uint32_t bytes = (uint32_t)nfl * 4u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+        const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+        asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(d), "l"(src), "r"(bytes), "r"(mb) : "memory");
+    }
+    const uint32_t parity = sm.phase & 1u;
+    if (threadIdx.x == 0) {
+        // bounded wait; after a timeout wait (bounded again) for the copy in flight to land
+        int ok = try_wait_bounded(mb, parity, p.timeout_ns);
+        if (!ok) {
+            atomicCAS(&p.ctrl->error, 0, RMB_ERR_BARRIER_TIMEOUT);
+            try_wait_bounded(mb, parity, p.timeout_ns);
+        }
+        sm.ok = ok;
+    }
+    __syncthreads();
+    const bool ok = sm.ok != 0;
+    if (ok && threadIdx.x != 0) try_wait_bounded(mb, parity, p.timeout_ns);   // completes at once
+    __syncthreads();
+    if (threadIdx.x == 0) sm.phase++;
+    return ok;
+}
+
+template <int KIND, bool VEC>
+__device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole, const float* A, int s,
+                            int pi_s, bool* ok)
+{
+    const int n = p.n;
+    const int nrows = pi_s >= 0 ? 1 : p.m;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    for (int a0 = 0; a0 < nrows; a0 += kDenseMB) {
+        float acc[kDenseMB];
+#pragma unroll
+        for (int u = 0; u < kDenseMB; ++u) acc[u] = 0.f;
+        const float* rows[kDenseMB];
+#pragma unroll
+        for (int u = 0; u < kDenseMB; ++u) {
+            const int a = pi_s >= 0 ? pi_s : min(a0 + u, p.m - 1);
+            rows[u] = p.P + ((int64_t)s * p.m + a) * (int64_t)n;
+        }
+        for (int c0 = 0; c0 < n; c0 += p.stage) {
+            const int clen = min(p.stage, n - c0);
+            if (!whole) {
+                __syncthreads();
+                if (!stage_values(p, sm, stage, A + c0, (clen + 3) & ~3)) { *ok = false; return Best{kInf, 0, kInf}; }
+            }
+            if (VEC) {
+                const float4* st4 = reinterpret_cast<const float4*>(stage);
+                for (int j4 = tid; j4 < (clen >> 2); j4 += blockDim.x) {
+                    const float4 v = st4[j4];
+#pragma unroll
+                    for (int u = 0; u < kDenseMB; ++u) {
+                        if (a0 + u < nrows) {
+                            const float4 pr = __ldcs(reinterpret_cast<const float4*>(rows[u] + c0) + j4);
+                            acc[u] = fmaf(pr.x, v.x, acc[u]);
+                            acc[u] = fmaf(pr.y, v.y, acc[u]);
+                            acc[u] = fmaf(pr.z, v.z, acc[u]);
+                            acc[u] = fmaf(pr.w, v.w, acc[u]);
+                        }
+                    }
+                }
+            } else {
+                for (int j = tid; j < clen; j += blockDim.x) {
+                    const float v = stage[j];
+#pragma unroll
+                    for (int u = 0; u < kDenseMB; ++u)
+                        if (a0 + u < nrows) acc[u] = fmaf(__ldcs(rows[u] + c0 + j), v, acc[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kDenseMB; ++u) {
+            float x = acc[u];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if (lane == 0) sm.red[wid][u] = x;
+        }
+        __syncthreads();
+        if (tid < kDenseMB && a0 + tid < nrows) {
+            float tot = 0.f;
+            for (int w = 0; w < nw; ++w) tot += sm.red[w][tid];
+            const int a = pi_s >= 0 ? pi_s : a0 + tid;
+            const float c = __ldg(p.cost + (int64_t)s * p.m + a);
+            sm.q[a0 + tid] = (c == kInf) ? kInf : fmaf(p.gamma, tot, c);
+        }
+        __syncthreads();
+    }
+    Best best = {kInf, 0x7fffffff, kInf};
+    if (tid == 0) {
+        for (int ai = 0; ai < nrows; ++ai) {
+            const Best cur = {sm.q[ai], pi_s >= 0 ? pi_s : ai, kInf};
+            best = better(best, cur);
+        }
+    }
+    return best;
+}
+
+template <int KIND, bool VEC>
+__device__ bool dense_batch(const KP& p, DenseSmem& sm, float* stage, const float* A, float* B, int pos0,
+                            int len, const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc,
+                            bool* perm_ok)
+{
+    const bool whole = p.n <= p.stage;
+    const int G = gridDim.x;
+    if ((int)blockIdx.x >= len) return true;
+    bool ok = true;
+    if (whole && !stage_values(p, sm, stage, A, (p.n + 3) & ~3)) return false;
+    for (int j0 = 0; (int)blockIdx.x + j0 * G < len; j0 += 32) {
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int pos = (int)blockIdx.x + (j0 + (int)threadIdx.x) * G;
+            int st = -1;
+            if (pos < len) st = K ? (int)perm_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
+            sm.perm[threadIdx.x] = st;
+        }
+        __syncthreads();
+        for (int jj = 0; jj < 32; ++jj) {
+            const int s = sm.perm[jj];
+            if (s < 0) break;
+            const int pi_s = (KIND == K_POLICY)
+                                 ? (int)min((uint32_t)ld_l2(p.pi_in ? p.pi_in + s : p.pi + s), (uint32_t)(p.m - 1))
+                                 : -1;
+            const Best r = dense_state<KIND, VEC>(p, sm, stage, whole, A, s, pi_s, &ok);
+            if (!ok) return false;
+            if (threadIdx.x == 0)
+                state_epilogue<KIND>(p, r, s, (int)blockIdx.x + (j0 + jj) * G, A, B, Sout, Wout, C, acc);
+        }
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------------------------------------
+// The persistent driver.
+// ------------------------------------------------------------------------------------------------
+struct RedSmem {
+    float v[3][32];
+    float bc[4];
+};
+
+__device__ __forceinline__ void publish(Ctrl* c, int slot, Acc a, RedSmem& rs)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) {
+        a.dmax = fmaxf(a.dmax, __shfl_xor_sync(0xffffffffu, a.dmax, off));
+        a.vlo = fminf(a.vlo, __shfl_xor_sync(0xffffffffu, a.vlo, off));
+        a.vhi = fmaxf(a.vhi, __shfl_xor_sync(0xffffffffu, a.vhi, off));
+    }
+    __syncthreads();
+    if (lane == 0) {
+        rs.v[0][wid] = a.dmax;
+        rs.v[1][wid] = a.vlo;
+        rs.v[2][wid] = a.vhi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {   // thread 0 already holds warp 0's values
+            a.dmax = fmaxf(a.dmax, rs.v[0][w]);
+            a.vlo = fminf(a.vlo, rs.v[1][w]);
+            a.vhi = fmaxf(a.vhi, rs.v[2][w]);
+        }
+        atomicMax(&c->red_delta[slot], __float_as_uint(a.dmax));
+        atomicMax(&c->red_hi[slot], okey(a.vhi));
+        atomicMax(&c->red_nlo[slot], okey(-a.vlo));
+    }
+}
+
+// read a reduction slot after a grid-wide wait; every thread of the CTA gets the same values
+__device__ __forceinline__ void read_slot(Ctrl* c, int slot, RedSmem& rs, float& dmax, float& lo, float& hi)
+{
+    if (threadIdx.x == 0) {
+        rs.bc[0] = __uint_as_float(ld_l2((const int*)&c->red_delta[slot]));
+        rs.bc[1] = -okey_inv((uint32_t)ld_l2((const int*)&c->red_nlo[slot]));
+        rs.bc[2] = okey_inv((uint32_t)ld_l2((const int*)&c->red_hi[slot]));
+    }
+    __syncthreads();
+    dmax = rs.bc[0];
+    lo = rs.bc[1];
+    hi = rs.bc[2];
+    __syncthreads();
+}
+
+template <int PATH>
+struct Runner {
+    const KP& p;
+    Ctrl* c;
+    unsigned long long target;
+    long long barriers;
+    bool stall;
+    int cur;
+    int red_epoch;
+    Centre C;
+    RedSmem& rs;
+    DenseSmem* dsm;
+    float* stage;
+    bool perm_ok;
+
+    __device__ Runner(const KP& kp, RedSmem& r, DenseSmem* d, float* st)
+        : p(kp), c(kp.ctrl), target(0), barriers(0), stall(false), cur(0), red_epoch(0), rs(r), dsm(d),
+          stage(st), perm_ok(true) {}
+
+    __device__ bool sync(int site)
+    {
+        const bool skip = stall;
+        stall = false;
+        if (!perm_ok) atomicCAS(&c->error, 0, RMB_ERR_UNSUPPORTED);
+        ++barriers;
+        return grid_wait(c, target, p.timeout_ns, skip, site);
+    }
+
+    __device__ size_t gtid() const { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
+    __device__ size_t gthreads() const { return (size_t)gridDim.x * blockDim.x; }
+
+    template <int KIND>
+    __device__ bool batch(const float* A, float* B, int pos0, int len, const PermKey* K, int32_t* So, float* Wo,
+                          Acc& acc)
+    {
+        if (PATH == PATH_DENSE) {
+            if (p.n % 4 == 0 && (((uintptr_t)p.P) & 15) == 0)
+                return dense_batch<KIND, true>(p, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+            return dense_batch<KIND, false>(p, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+        } else {
+            const int lps = (KIND == K_POLICY) ? p.lps_one : p.lps_all;
+            csr_batch<KIND, PATH == PATH_CSR_VEC>(p, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+            return true;
+        }
+    }
+
+    __device__ void copy_batch(const int32_t* S, const float* Wv, int len, float* B)
+    {
+        for (size_t i = gtid(); i < (size_t)len; i += gthreads()) st_l2(B + ld_l2(S + i), ld_l2(Wv + i));
+    }
+
+    // Re-centre between sweeps when the midpoint of the values moved by more than a quarter of
+    // their spread: mu += shift, d -= shift in the buffer that holds the complete values (and the
+    // other buffer gets the same, which also completes the end-of-sweep copy).
+    __device__ float shift_for(float lo, float hi) const
+    {
+        const float mid = 0.5f * (lo + hi);
+        const float spread = hi - lo;
+        const float floor_ = 1e-6f * (float)(fabs(C.mu) + 1.0);
+        if (!(fabsf(mid) > fmaxf(0.25f * spread, floor_))) return 0.f;
+        return mid;
+    }
+
+    // One sweep of B_b (KIND K_MIN) or B_{pi,b} (K_POLICY).  Returns false on failure; sets stop.
+    // can_stop: VI / evaluation (may end after this sweep); MPI evaluation sweeps always complete
+    template <int KIND>
+    __device__ bool sweep(long long k, long long j, bool can_stop, bool is_last, bool& stop, float& delta)
+    {
+        PermKey K;
+        K.n = (uint32_t)p.n;
+        K.h = p.h;
+        K.mask = (1u << p.h) - 1u;
+        K.k0 = p.seed_lo;
+        K.k1 = p.seed_hi;
+        K.s_lo = (uint32_t)(unsigned long long)k;
+        K.s_hi = (uint32_t)((unsigned long long)k >> 32);
+        const int slot = red_epoch % 3;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const int nxt = (red_epoch + 1) % 3;
+            c->red_delta[nxt] = 0u;
+            c->red_hi[nxt] = 0u;
+            c->red_nlo[nxt] = 0u;
+        }
+        ++red_epoch;
+        Acc acc = {0.f, kInf, -kInf};
+        for (int t = 0; t < p.T; ++t) {
+            float* A = p.d[(cur + t) & 1];
+            float* B = p.d[(cur + t + 1) & 1];
+            if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B);
+            const int len = (t == p.T - 1) ? p.last_len : p.b;
+            if (!batch<KIND>(A, B, t * p.b, len, &K, p.S[t & 1], p.W[t & 1], acc)) return false;
+            if (t == p.T - 1) publish(c, slot, acc, rs);
+            if (!sync(10 + (t & 1))) return false;
+        }
+        float lo, hi;
+        read_slot(c, slot, rs, delta, lo, hi);
+        const int newcur = (cur + p.T) & 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace && j >= 0) p.trace[j] = (double)delta;
+        stop = can_stop && ((double)delta <= p.eps || is_last);
+        if (delta != delta) {
+            atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
+            return false;
+        }
+        cur = newcur;
+        if (stop) return true;
+        const float shift = shift_for(lo, hi);
+        if (shift != 0.f) {
+            float* F = p.d[cur];
+            float* O = p.d[cur ^ 1];
+            for (size_t i = gtid(); i < (size_t)p.n; i += gthreads()) {
+                const float v = ld_l2(F + i) - shift;
+                st_l2(F + i, v);
+                st_l2(O + i, v);
+            }
+            C = make_centre(C.mu + (double)shift, p.gamma_d);
+            if (!sync(20)) return false;
+        } else if (p.T >= 2) {
+            copy_batch(p.S[(p.T - 1) & 1], p.W[(p.T - 1) & 1], p.last_len, p.d[cur ^ 1]);
+            if (!sync(21)) return false;
+        }
+        return true;
+    }
+
+    // Full Bellman pass at the current values: greedy policy, Q-gap, TV, ||TV - V||_inf, V out.
+    __device__ bool greedy_pass(float& resid)
+    {
+        const int slot = red_epoch % 3;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            const int nxt = (red_epoch + 1) % 3;
+            c->red_delta[nxt] = 0u;
+            c->red_hi[nxt] = 0u;
+            c->red_nlo[nxt] = 0u;
+        }
+        ++red_epoch;
+        Acc acc = {0.f, kInf, -kInf};
+        const float* A = p.d[cur];
+        if (!batch<K_GREEDY>(A, nullptr, 0, p.n, nullptr, nullptr, nullptr, acc)) return false;
+        publish(c, slot, acc, rs);
+        if (!sync(30)) return false;
+        float lo, hi;
+        read_slot(c, slot, rs, resid, lo, hi);
+        if (resid != resid) {
+            atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
+            return false;
+        }
+        return true;
+    }
+
+    __device__ void write_values()
+    {
+        const float* F = p.d[cur];
+        for (size_t i = gtid(); i < (size_t)p.n; i += gthreads()) p.Vout[i] = (float)(C.mu + (double)ld_l2(F + i));
+    }
+
+    __device__ void run()
+    {
+        stall = (p.flags & RMB_FLAG_INJECT_BARRIER_STALL) && blockIdx.x == 0;
+        if (PATH == PATH_DENSE && threadIdx.x == 0) {
+            const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&dsm->mbar);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            dsm->phase = 0;
+        }
+        __syncthreads();
+        if (ld_volatile(&c->error) != 0) return;   // the validation pass rejected the MDP
+
+        // set-up: centre on the midpoint of the start values
+        Acc a0 = {0.f, kInf, -kInf};
+        for (size_t i = gtid(); i < (size_t)p.n; i += gthreads()) {
+            const float v = p.Vin[i];
+            a0.vlo = fminf(a0.vlo, v);
+            a0.vhi = fmaxf(a0.vhi, v);
+            if (v != v || fabsf(v) == kInf) atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
+        }
+        publish(c, 3, a0, rs);
+        if (!sync(1)) return finish(false, 0, 0, 0.0);
+        float dm, lo, hi;
+        read_slot(c, 3, rs, dm, lo, hi);
+        const double mu0 = (double)(float)(0.5 * ((double)lo + (double)hi));
+        C = make_centre(mu0, p.gamma_d);
+        for (size_t i = gtid(); i < (size_t)p.n; i += gthreads()) {
+            const float v = (float)((double)p.Vin[i] - mu0);
+            st_l2(p.d[0] + i, v);
+            st_l2(p.d[1] + i, v);
+        }
+        if (!sync(2)) return finish(false, 0, 0, 0.0);
+        cur = 0;
+
+        long long sweeps = 0, iters = 0;
+        double residual = 0.0;
+        bool converged = false;
+        if (p.mode == MODE_GREEDY) {
+            float r;
+            if (!greedy_pass(r)) return finish(false, 0, 0, 0.0);
+            return finish(true, 0, 0, (double)r, true);
+        }
+        if (p.mode == MODE_VI || p.mode == MODE_EVAL) {
+            for (long long j = 0; j < p.max_sweeps; ++j) {
+                bool stop = false;
+                float delta = 0.f;
+                const bool last = j + 1 == p.max_sweeps;
+                const bool ok = (p.mode == MODE_VI)
+                                    ? sweep<K_MIN>(p.start_sweep + j, j, true, last, stop, delta)
+                                    : sweep<K_POLICY>(p.start_sweep + j, j, true, last, stop, delta);
+                if (!ok) return finish(false, sweeps, 0, 0.0);
+                ++sweeps;
+                residual = (double)delta;
+                if (stop) {
+                    converged = (double)delta <= p.eps;
+                    break;
+                }
+            }
+            if (p.mode == MODE_VI && (p.pi || p.qgap)) {
+                float r;
+                if (!greedy_pass(r)) return finish(false, sweeps, 0, residual);   // also writes V
+            } else {
+                write_values();
+            }
+            return finish(true, sweeps, 0, residual, converged);
+        }
+        // MODE_MPI (Alg. 1): improvement pass, stop test, K evaluation sweeps of B_{pi,b}
+        for (;;) {
+            float r;
+            if (!greedy_pass(r)) return finish(false, sweeps, iters, residual);   // also writes V
+            residual = (double)r;
+            if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace) p.trace[iters] = residual;
+            ++iters;
+            if (residual <= p.eps) { converged = true; break; }
+            if (iters >= p.max_sweeps) break;
+            for (int e = 0; e < p.K; ++e) {
+                bool stop = false;
+                float delta = 0.f;
+                if (!sweep<K_POLICY>(p.start_sweep + sweeps, -1, false, false, stop, delta))
+                    return finish(false, sweeps, iters, residual);
+                ++sweeps;
+            }
+        }
+        return finish(true, sweeps, iters, residual, converged);
+    }
+
+    __device__ void finish(bool ok, long long sweeps, long long iters, double residual, bool converged = false)
+    {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->sweeps = sweeps;
+            c->iters = iters;
+            c->barriers = barriers;
+            c->residual = residual;
+            c->mu = C.mu;
+            int st = ld_volatile(&c->error);
+            if (ok && st == 0 && !converged) st = RMB_ERR_NOT_CONVERGED;
+            c->status = st;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kCsrThreads, 2) rmb_csr_vec_kernel(KP p)
+{
+    __shared__ RedSmem rs;
+    Runner<PATH_CSR_VEC> R(p, rs, nullptr, nullptr);
+    R.run();
+}
+
+__global__ void __launch_bounds__(kCsrThreads, 2) rmb_csr_gen_kernel(KP p)
+{
+    __shared__ RedSmem rs;
+    Runner<PATH_CSR_GEN> R(p, rs, nullptr, nullptr);
+    R.run();
+}
+
+__global__ void __launch_bounds__(kDenseThreads, 3) rmb_dense_kernel(KP p)
+{
+    __shared__ RedSmem rs;
+    __shared__ __align__(16) DenseSmem dsm;
+    extern __shared__ __align__(128) float stage[];
+    Runner<PATH_DENSE> R(p, rs, &dsm, stage);
+    R.run();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Permutation and validation kernels.
+// ------------------------------------------------------------------------------------------------
+__global__ void rmb_perm_kernel(uint32_t n, uint32_t h, uint32_t k0, uint32_t k1, uint32_t s_lo, uint32_t s_hi,
+                                int32_t* out)
+{
+    PermKey K{n, h, (1u << h) - 1u, k0, k1, s_lo, s_hi};
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
+        bool ok = true;
+        const uint32_t x = perm_at((uint32_t)p, K, &ok);
+        out[p] = ok ? (int32_t)x : -1;   // -1 cannot occur for a bijection; marks a broken walk
+    }
+}
+
+struct VP {
+    int n, m, k, fmt;
+    const float* P;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* prob;
+    const float* cost;
+    int* err;
+};
+
+__global__ void rmb_validate_kernel(VP v)
+{
+    const int lane = threadIdx.x & 31;
+    const size_t warp = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const size_t nwarps = ((size_t)gridDim.x * blockDim.x) >> 5;
+    const size_t rows = (size_t)v.n * v.m;
+    bool bad = false;
+    for (size_t r = warp; r < rows; r += nwarps) {
+        const float c = v.cost[r];
+        if (c != c || c == -kInf) bad = true;
+        const bool admissible = c != kInf;
+        float sum = 0.f;
+        if (v.fmt == RMB_CSR) {
+            const int64_t e0 = v.row_ptr[r], e1 = v.row_ptr[r + 1];
+            if (e0 < 0 || e1 < e0) { bad = true; continue; }
+            if (v.k > 0 && (e0 != (int64_t)r * v.k || e1 != (int64_t)(r + 1) * v.k)) bad = true;
+            for (int64_t e = e0 + lane; e < e1; e += 32) {
+                const float pr = v.prob[e];
+                const int j = v.col[e];
+                if (!(pr >= 0.f && pr <= 1.f)) bad = true;
+                if (j < 0 || j >= v.n) bad = true;
+                sum += pr;
+            }
+        } else {
+            const float* row = v.P + r * (size_t)v.n;
+            for (int j = lane; j < v.n; j += 32) {
+                const float pr = row[j];
+                if (!(pr >= 0.f && pr <= 1.f)) bad = true;
+                sum += pr;
+            }
+        }
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (admissible && !(fabsf(sum - 1.f) <= 1e-4f)) bad = true;
+    }
+    // every state needs one admissible action
+    for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < (size_t)v.n;
+         s += (size_t)gridDim.x * blockDim.x) {
+        bool any = false;
+        for (int a = 0; a < v.m; ++a) any |= (v.cost[s * v.m + a] != kInf);
+        if (!any) bad = true;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && v.fmt == RMB_CSR && v.row_ptr[0] != 0) bad = true;
+    if (bad) atomicCAS(v.err, 0, RMB_ERR_INVALID_MDP);
+}
+
+}  // namespace rmb
+
+// ==================================================================================================
+// Host side
+// ==================================================================================================
+using namespace rmb;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+
+struct DevInfo {
+    int sms = 0;
+    int occ_csr_vec = 0, occ_csr_gen = 0;
+    bool init = false;
+};
+DevInfo g_dev[64];
+std::mutex g_mu;
+
+int dev_info(DevInfo** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RMB_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevInfo& d = g_dev[dev];
+    if (!d.init) {
+        if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RMB_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_csr_vec, rmb_csr_vec_kernel, kCsrThreads, 0) != cudaSuccess)
+            return RMB_ERR_CUDA;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_csr_gen, rmb_csr_gen_kernel, kCsrThreads, 0) != cudaSuccess)
+            return RMB_ERR_CUDA;
+        d.init = true;
+    }
+    *out = &d;
+    return RMB_OK;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Layout {
+    size_t ctrl, d0, d1, s0, s1, w0, w1, total;
+};
+
+Layout layout(int64_t n, int64_t b)
+{
+    Layout L;
+    const size_t nb = align_up((size_t)n * 4, 256);
+    const size_t bb = align_up((size_t)b * 4, 256);
+    L.ctrl = 0;
+    L.d0 = align_up(sizeof(Ctrl), 256);
+    L.d1 = L.d0 + nb;
+    L.s0 = L.d1 + nb;
+    L.s1 = L.s0 + bb;
+    L.w0 = L.s1 + bb;
+    L.w1 = L.w0 + bb;
+    L.total = L.w1 + bb;
+    return L;
+}
+
+int check_mdp(const rmb_mdp* M)
+{
+    if (!M) return RMB_ERR_ARG;
+    if (M->n < 1 || M->m < 1) return RMB_ERR_ARG;
+    if (M->n >= ((int64_t)1 << 31)) return RMB_ERR_UNSUPPORTED;
+    if (!(M->gamma > 0.0 && M->gamma < 1.0)) return RMB_ERR_ARG;
+    if (!M->cost) return RMB_ERR_ARG;
+    if (M->format == RMB_DENSE) {
+        if (!M->P) return RMB_ERR_ARG;
+        if (M->m > kDenseMaxM) return RMB_ERR_UNSUPPORTED;
+    } else if (M->format == RMB_CSR) {
+        if (!M->row_ptr || !M->col || !M->prob) return RMB_ERR_ARG;
+        if (M->k_uniform < 0) return RMB_ERR_ARG;
+    } else {
+        return RMB_ERR_ARG;
+    }
+    return RMB_OK;
+}
+
+int effective_batch(const rmb_mdp* M, const rmb_opts* O, int64_t* b)
+{
+    if (!O || O->batch < 1) return RMB_ERR_ARG;
+    *b = O->batch > M->n ? M->n : O->batch;
+    return RMB_OK;
+}
+
+bool csr_vec_ok(const rmb_mdp* M)
+{
+    if (M->format != RMB_CSR || M->k_uniform <= 0 || (M->k_uniform & 3)) return false;
+    const int k4 = M->k_uniform >> 2;
+    const bool pow2 = (k4 & (k4 - 1)) == 0;
+    if (!(pow2 || k4 % 32 == 0)) return false;
+    if (((uintptr_t)M->prob & 15) || ((uintptr_t)M->col & 15)) return false;
+    return true;
+}
+
+int pow2ceil(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+struct Call {
+    int mode;
+    const rmb_mdp* M;
+    const rmb_opts* O;
+    const float* Vin;
+    float* Vout;
+    float* TV;
+    int32_t* pi;
+    float* qgap;
+    const int32_t* pi_in;
+    void* ws;
+    size_t ws_bytes;
+    rmb_stats* stats;
+    cudaStream_t stream;
+};
+
+int launch_validate(const rmb_mdp* M, int* err, cudaStream_t st, int sms)
+{
+    VP v;
+    v.n = (int)M->n;
+    v.m = M->m;
+    v.k = M->format == RMB_CSR ? M->k_uniform : 0;
+    v.fmt = M->format;
+    v.P = M->P;
+    v.row_ptr = M->row_ptr;
+    v.col = M->col;
+    v.prob = M->prob;
+    v.cost = M->cost;
+    v.err = err;
+    rmb_validate_kernel<<<sms * 4, 256, 0, st>>>(v);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
+}
+
+int solve(const Call& q)
+{
+    int st = check_mdp(q.M);
+    if (st) return st;
+    const rmb_mdp* M = q.M;
+    const rmb_opts* O = q.O;
+    if (!O) return RMB_ERR_ARG;
+    int64_t b = M->n;
+    if (q.mode != MODE_GREEDY) {
+        if ((st = effective_batch(M, O, &b))) return st;
+        if (O->max_sweeps < 1) return RMB_ERR_ARG;
+        if (!(O->eps >= 0.0) || std::isinf(O->eps)) return RMB_ERR_ARG;
+        if (q.mode == MODE_MPI && (O->eval_sweeps < 1 || !q.pi)) return RMB_ERR_ARG;
+        if (q.mode == MODE_EVAL && !q.pi_in) return RMB_ERR_ARG;
+        if (O->start_sweep < 0) return RMB_ERR_ARG;
+    }
+    if (!q.Vin) return RMB_ERR_ARG;
+    if (O->grid_ctas < 0 || O->barrier_timeout_ns < 0) return RMB_ERR_ARG;
+    const Layout L = layout(M->n, b);
+    if (!q.ws || ((uintptr_t)q.ws & 255)) return RMB_ERR_WORKSPACE;
+    if (q.ws_bytes < L.total) return RMB_ERR_WORKSPACE;
+
+    DevInfo* D = nullptr;
+    if ((st = dev_info(&D))) return st;
+
+    char* ws = static_cast<char*>(q.ws);
+    KP p;
+    std::memset(&p, 0, sizeof(p));
+    p.n = (int)M->n;
+    p.m = M->m;
+    p.k = M->format == RMB_CSR ? M->k_uniform : 0;
+    p.P = M->P;
+    p.row_ptr = M->row_ptr;
+    p.col = M->col;
+    p.prob = M->prob;
+    p.cost = M->cost;
+    p.gamma = (float)M->gamma;
+    p.gamma_d = M->gamma;
+    p.mode = q.mode;
+    p.b = (int)b;
+    p.T = (int)((M->n + b - 1) / b);
+    p.last_len = (int)(M->n - (int64_t)(p.T - 1) * b);
+    p.K = O->eval_sweeps;
+    p.start_sweep = O->start_sweep;
+    p.max_sweeps = q.mode == MODE_GREEDY ? 0 : O->max_sweeps;
+    p.eps = O->eps;
+    p.seed_lo = (uint32_t)O->seed;
+    p.seed_hi = (uint32_t)(O->seed >> 32);
+    p.h = perm_half_bits(M->n);
+    p.Vin = q.Vin;
+    p.Vout = q.Vout;
+    p.TVout = q.TV;
+    p.pi = q.pi;
+    p.qgap = q.qgap;
+    p.pi_in = q.pi_in;
+    p.d[0] = reinterpret_cast<float*>(ws + L.d0);
+    p.d[1] = reinterpret_cast<float*>(ws + L.d1);
+    p.S[0] = reinterpret_cast<int32_t*>(ws + L.s0);
+    p.S[1] = reinterpret_cast<int32_t*>(ws + L.s1);
+    p.W[0] = reinterpret_cast<float*>(ws + L.w0);
+    p.W[1] = reinterpret_cast<float*>(ws + L.w1);
+    p.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
+    p.trace = q.mode == MODE_GREEDY ? nullptr : O->trace;
+    p.timeout_ns = O->barrier_timeout_ns > 0 ? O->barrier_timeout_ns : 2000000000LL;
+    p.flags = O->flags;
+
+    int path;
+    if (M->format == RMB_DENSE) path = PATH_DENSE;
+    else if (csr_vec_ok(M)) path = PATH_CSR_VEC;
+    else path = PATH_CSR_GEN;
+    p.path = path;
+    if (path == PATH_CSR_VEC) {
+        const int k4 = p.k >> 2;
+        const int cpr = k4 < 32 ? k4 : 32;
+        p.lps_one = cpr;
+        int all = pow2ceil(cpr * p.m);
+        p.lps_all = all > 32 ? 32 : all;
+    } else {
+        p.lps_one = 32;
+        p.lps_all = 32;
+    }
+
+    const void* fn;
+    int threads, per_sm;
+    size_t smem = 0;
+    if (path == PATH_DENSE) {
+        fn = reinterpret_cast<const void*>(rmb_dense_kernel);
+        threads = kDenseThreads;
+        int max_stage = kDenseMaxStage;
+        if (const char* e = std::getenv("RMB_DENSE_STAGE")) {   // tuning / test knob: floats staged at once
+            const int v = std::atoi(e);
+            if (v >= 4 && v <= kDenseMaxStage) max_stage = v & ~3;
+        }
+        p.stage = M->n <= max_stage ? (int)((M->n + 3) & ~3LL) : max_stage;
+        smem = (size_t)p.stage * 4;
+        if (cudaFuncSetAttribute(rmb_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return RMB_ERR_CUDA;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rmb_dense_kernel, threads, smem) != cudaSuccess)
+            return RMB_ERR_CUDA;
+        per_sm = occ < 2 ? occ : 2;
+    } else {
+        fn = path == PATH_CSR_VEC ? reinterpret_cast<const void*>(rmb_csr_vec_kernel)
+                                  : reinterpret_cast<const void*>(rmb_csr_gen_kernel);
+        threads = kCsrThreads;
+        const int occ = path == PATH_CSR_VEC ? D->occ_csr_vec : D->occ_csr_gen;
+        per_sm = occ < 4 ? occ : 4;
+    }
+    if (per_sm < 1) return RMB_ERR_CUDA;
+    const int max_grid = per_sm * D->sms;
+    int grid = O->grid_ctas > 0 ? O->grid_ctas : max_grid;
+    if (grid > max_grid) grid = max_grid;
+
+    cudaStream_t s = q.stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (q.stats) {
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMB_ERR_CUDA;
+        cudaEventRecord(e0, s);
+    }
+    if (cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return RMB_ERR_CUDA;
+    if (O->validate && (st = launch_validate(M, &p.ctrl->error, s, D->sms))) return st;
+    void* args[] = {&p};
+    cudaError_t ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+    g_launches++;
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return RMB_ERR_CUDA;
+    }
+    if (!q.stats) return RMB_OK;
+    cudaEventRecord(e1, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
+    Ctrl h;
+    if (cudaMemcpy(&h, p.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) return RMB_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::memset(q.stats, 0, sizeof(rmb_stats));
+    q.stats->sweeps = h.sweeps;
+    q.stats->iters = h.iters;
+    q.stats->barriers = h.barriers;
+    q.stats->residual = h.residual;
+    q.stats->v_shift = h.mu;
+    q.stats->status = h.status != 0 ? h.status : h.error;
+    q.stats->grid_ctas = grid;
+    q.stats->path = path;
+    q.stats->lanes_per_state = path == PATH_DENSE ? threads : p.lps_all;
+    q.stats->ms = ms;
+    return q.stats->status;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t rmb_workspace_bytes(const rmb_mdp* mdp, const rmb_opts* opts)
+{
+    if (check_mdp(mdp)) return 0;
+    int64_t b = mdp->n;
+    if (opts && opts->batch >= 1) b = opts->batch > mdp->n ? mdp->n : opts->batch;
+    return layout(mdp->n, b).total;
+}
+
+int rmb_vi(const rmb_mdp* mdp, const rmb_opts* opts, float* V_inout, int32_t* pi_out, float* qgap_out,
+           void* workspace, size_t workspace_bytes, rmb_stats* stats, void* stream)
+{
+    Call q{MODE_VI, mdp, opts, V_inout, V_inout, nullptr, pi_out, qgap_out, nullptr,
+           workspace, workspace_bytes, stats, static_cast<cudaStream_t>(stream)};
+    return solve(q);
+}
+
+int rmb_mpi(const rmb_mdp* mdp, const rmb_opts* opts, float* V_inout, int32_t* pi_out, float* qgap_out,
+            void* workspace, size_t workspace_bytes, rmb_stats* stats, void* stream)
+{
+    Call q{MODE_MPI, mdp, opts, V_inout, V_inout, nullptr, pi_out, qgap_out, nullptr,
+           workspace, workspace_bytes, stats, static_cast<cudaStream_t>(stream)};
+    return solve(q);
+}
+
+int rmb_eval_policy(const rmb_mdp* mdp, const int32_t* pi, const rmb_opts* opts, float* V_inout,
+                    void* workspace, size_t workspace_bytes, rmb_stats* stats, void* stream)
+{
+    Call q{MODE_EVAL, mdp, opts, V_inout, V_inout, nullptr, nullptr, nullptr, pi,
+           workspace, workspace_bytes, stats, static_cast<cudaStream_t>(stream)};
+    return solve(q);
+}
+
+int rmb_greedy(const rmb_mdp* mdp, const rmb_opts* opts, const float* V, float* TV_out, int32_t* pi_out,
+               float* qgap_out, void* workspace, size_t workspace_bytes, rmb_stats* stats, void* stream)
+{
+    Call q{MODE_GREEDY, mdp, opts, V, nullptr, TV_out, pi_out, qgap_out, nullptr,
+           workspace, workspace_bytes, stats, static_cast<cudaStream_t>(stream)};
+    return solve(q);
+}
+
+int rmb_permutation(int64_t n, uint64_t seed, uint64_t sweep, int32_t* out, void* stream)
+{
+    if (n < 1 || !out) return RMB_ERR_ARG;
+    if (n >= ((int64_t)1 << 31)) return RMB_ERR_UNSUPPORTED;
+    DevInfo* D = nullptr;
+    int st = dev_info(&D);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)D->sms * 8);
+    rmb_perm_kernel<<<blocks, 256, 0, s>>>((uint32_t)n, perm_half_bits(n), (uint32_t)seed, (uint32_t)(seed >> 32),
+                                           (uint32_t)sweep, (uint32_t)(sweep >> 32), out);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
+}
+
+int rmb_validate(const rmb_mdp* mdp, void* workspace, size_t workspace_bytes, void* stream)
+{
+    int st = check_mdp(mdp);
+    if (st) return st;
+    if (!workspace || ((uintptr_t)workspace & 255) || workspace_bytes < 256) return RMB_ERR_WORKSPACE;
+    DevInfo* D = nullptr;
+    if ((st = dev_info(&D))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int* err = static_cast<int*>(workspace);
+    if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return RMB_ERR_CUDA;
+    if ((st = launch_validate(mdp, err, s, D->sms))) return st;
+    int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RMB_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
+    return h;
+}
+
+const char* rmb_status_string(int status)
+{
+    switch (status) {
+    case RMB_OK: return "ok";
+    case RMB_ERR_ARG: return "invalid argument";
+    case RMB_ERR_CUDA: return "CUDA runtime error";
+    case RMB_ERR_NOT_CONVERGED: return "not converged within the sweep limit";
+    case RMB_ERR_BARRIER_TIMEOUT: return "grid-wide wait timed out";
+    case RMB_ERR_INVALID_MDP: return "invalid MDP (probability, index, row sum or cost)";
+    case RMB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case RMB_ERR_UNSUPPORTED: return "unsupported size or layout";
+    case RMB_ERR_NONFINITE: return "non-finite value";
+    default: return "unknown status";
+    }
+}
+
+uint64_t rmb_kernel_launches(void) { return g_launches.load(); }
+
+int rmb_version(void) { return (1 << 16) | 0; }
+
+}  // extern "C"

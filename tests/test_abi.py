@@ -1,0 +1,153 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function include/rmb.h declares,
+its structs have the header's layout, and argument errors come back before anything touches CUDA."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import paper_2110_02901_b300 as rmb
+from paper_2110_02901_b300 import build as rbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rmb.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    rbuild.build()
+    return rmb.lib()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rmb_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("rmb_vi", "rmb_mpi", "rmb_eval_policy", "rmb_greedy", "rmb_permutation", "rmb_validate",
+              "rmb_workspace_bytes", "rmb_status_string", "rmb_kernel_launches", "rmb_version"):
+        assert f in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    out = subprocess.run(["nm", "-D", "--defined-only", rmb.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (rmb_\w+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in declared_functions():
+        assert hasattr(L, f)
+
+
+def test_struct_layouts_match_header():
+    code = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "rmb.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rmb_mdp), sizeof(rmb_opts), sizeof(rmb_stats),
+         offsetof(rmb_mdp, gamma), offsetof(rmb_mdp, k_uniform), offsetof(rmb_opts, trace),
+         offsetof(rmb_stats, ms), offsetof(rmb_opts, flags));
+  return 0;
+}'''
+    d = tempfile.mkdtemp()
+    c = os.path.join(d, "t.c")
+    open(c, "w").write(code)
+    exe = os.path.join(d, "t")
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+    vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    mine = [ctypes.sizeof(rmb.rmb_mdp), ctypes.sizeof(rmb.rmb_opts), ctypes.sizeof(rmb.rmb_stats),
+            rmb.rmb_mdp.gamma.offset, rmb.rmb_mdp.k_uniform.offset, rmb.rmb_opts.trace.offset,
+            rmb.rmb_stats.ms.offset, rmb.rmb_opts.flags.offset]
+    assert vals == mine
+
+
+def test_status_strings_and_version(L):
+    assert rmb.rmb_status_string(0) == "ok"
+    assert "wait timed out" in rmb.rmb_status_string(rmb.RMB_ERR_BARRIER_TIMEOUT)
+    assert rmb.rmb_status_string(12345) == "unknown status"
+    assert L.rmb_version() >> 16 == 1
+
+
+def _fake_mdp(n=100, m=4, gamma=0.9, fmt=rmb.RMB_CSR):
+    d = rmb.rmb_mdp()
+    d.n, d.m, d.gamma, d.format = n, m, gamma, fmt
+    # non-null stand-in addresses: every call below is rejected before any pointer is used
+    d.cost = d.row_ptr = d.col = d.prob = d.P = 4096
+    d.k_uniform = 0
+    return d
+
+
+def _opts(b=10, max_sweeps=10, eps=1e-6):
+    return rmb.Opts(batch=b, max_sweeps=max_sweeps, eps=eps).desc()
+
+
+@pytest.mark.parametrize("bad", ["null_mdp", "n0", "m0", "gamma1", "gamma0", "fmt", "b0", "sweeps0", "eps_neg",
+                                 "eps_nan", "no_v", "ws_null", "ws_misaligned", "ws_small", "n_huge", "no_cost"])
+def test_argument_errors_need_no_gpu(L, bad):
+    d, o = _fake_mdp(), _opts()
+    V, ws, wsb = 4096, 8192, 1 << 30
+    mdp_ptr = ctypes.byref(d)
+    if bad == "null_mdp":
+        mdp_ptr = None
+    elif bad == "n0":
+        d.n = 0
+    elif bad == "m0":
+        d.m = 0
+    elif bad == "gamma1":
+        d.gamma = 1.0
+    elif bad == "gamma0":
+        d.gamma = 0.0
+    elif bad == "fmt":
+        d.format = 7
+    elif bad == "b0":
+        o.batch = 0
+    elif bad == "sweeps0":
+        o.max_sweeps = 0
+    elif bad == "eps_neg":
+        o.eps = -1.0
+    elif bad == "eps_nan":
+        o.eps = float("nan")
+    elif bad == "no_v":
+        V = None
+    elif bad == "ws_null":
+        ws = None
+    elif bad == "ws_misaligned":
+        ws = 8192 + 16
+    elif bad == "ws_small":
+        wsb = 16
+    elif bad == "n_huge":
+        d.n = 1 << 31
+    elif bad == "no_cost":
+        d.cost = None
+    st = L.rmb_vi(mdp_ptr, ctypes.byref(o), V, None, None, ws, wsb, None, None)
+    want = {"ws_null": rmb.RMB_ERR_WORKSPACE, "ws_misaligned": rmb.RMB_ERR_WORKSPACE,
+            "ws_small": rmb.RMB_ERR_WORKSPACE, "n_huge": rmb.RMB_ERR_UNSUPPORTED}.get(bad, rmb.RMB_ERR_ARG)
+    assert st == want
+
+
+def test_mpi_and_eval_require_their_policy_arrays(L):
+    d, o = _fake_mdp(), _opts()
+    o.eval_sweeps = 5
+    assert L.rmb_mpi(ctypes.byref(d), ctypes.byref(o), 4096, None, None, 8192, 1 << 30, None, None) == rmb.RMB_ERR_ARG
+    o.eval_sweeps = 0
+    assert L.rmb_mpi(ctypes.byref(d), ctypes.byref(o), 4096, 4096, None, 8192, 1 << 30, None, None) == rmb.RMB_ERR_ARG
+    assert L.rmb_eval_policy(ctypes.byref(d), None, ctypes.byref(o), 4096, 8192, 1 << 30, None, None) == rmb.RMB_ERR_ARG
+    assert L.rmb_permutation(0, 1, 2, 4096, None) == rmb.RMB_ERR_ARG
+    assert L.rmb_permutation(10, 1, 2, None, None) == rmb.RMB_ERR_ARG
+
+
+def test_workspace_size_formula(L):
+    d = _fake_mdp(n=1000)
+    o = _opts(b=64)
+    nb = L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o))
+    # control block + two value buffers + two position caches + two value caches, 256-byte aligned
+    assert nb == 256 + 2 * 4096 + 4 * 256
+    o.batch = 5000          # b > n means b = n
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 256 + 6 * 4096
+    d.gamma = 2.0
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 0
