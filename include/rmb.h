@@ -49,7 +49,9 @@ typedef enum {
     RMB_ERR_INVALID_MDP = -5,      /* device validation: bad probability, index, row sum or cost */
     RMB_ERR_WORKSPACE = -6,        /* workspace NULL, too small or not 256-byte aligned */
     RMB_ERR_UNSUPPORTED = -7,      /* a size this build does not handle (n >= 2^31, ...) */
-    RMB_ERR_NONFINITE = -8         /* a value became NaN during the solve */
+    RMB_ERR_NONFINITE = -8,        /* a value became NaN during the solve */
+    RMB_ERR_TOO_LARGE = -9         /* rmb_vi_noalloc: the solve needs more scratch than
+                                      RMB_NOALLOC_SCRATCH_BYTES */
 } rmb_status;
 
 enum { RMB_DENSE = 0, RMB_CSR = 1 };
@@ -172,6 +174,34 @@ int rmb_permutation(int64_t n, uint64_t seed, uint64_t sweep, int32_t *out, void
  *   workspace: at least 256 bytes (its first 256 bytes are used).
  */
 int rmb_validate(const rmb_mdp *mdp, void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * MB-VI exactly as rmb_vi, for callers that cannot allocate device memory.  The paper has no
+ * counterpart; this is a deployment convenience.
+ *
+ * Who needs it: code that only ever receives device pointers for its inputs and outputs from a host
+ * application that owns all device memory (a plugin inside a simulator, a solver embedded in a
+ * serving process, a pure C caller with no allocator handle), and control loops that forbid device
+ * allocation after start-up because cudaMalloc can synchronise the device and take unbounded time.
+ *
+ * Instead of a caller-provided workspace it uses one fixed scratch array of
+ * RMB_NOALLOC_SCRATCH_BYTES (8 MiB) compiled into the library as a file-scope __device__ array;
+ * every GPU that loads the library holds that array until the process exits.  A solve needs
+ * rmb_workspace_bytes(mdp, opts) of scratch (about 8*n + 16*min(b,n) bytes); larger problems are
+ * rejected with RMB_ERR_TOO_LARGE before anything is launched.  The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine, no CUDA events.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * Sharing: every call on a device uses the same array, which keeps the previous call's contents
+ * (each call clears the parts that must start at zero).  Calls that overlap on the GPU -- on
+ * different streams or from different host threads -- race on the array and give wrong results;
+ * serialise them.
+ * stats (optional): as for rmb_vi except ms = 0, grid_ctas = 0, path = -1, lanes_per_state = 0.
+ */
+#define RMB_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+int rmb_vi_noalloc(const rmb_mdp *mdp, const rmb_opts *opts, float *V_inout, int32_t *pi_out,
+                   float *qgap_out, rmb_stats *stats, void *stream);
 
 /* Static text for a status code. */
 const char *rmb_status_string(int status);

@@ -29,6 +29,8 @@ RMB_ERR_INVALID_MDP = -5
 RMB_ERR_WORKSPACE = -6
 RMB_ERR_UNSUPPORTED = -7
 RMB_ERR_NONFINITE = -8
+RMB_ERR_TOO_LARGE = -9
+RMB_NOALLOC_SCRATCH_BYTES = 8 << 20
 RMB_DENSE = 0
 RMB_CSR = 1
 RMB_FLAG_INJECT_BARRIER_STALL = 1
@@ -271,6 +273,29 @@ def rmb_greedy(mdp: DeviceMDP, V, TV=None, pi=None, qgap=None, opts: Optional[Op
     st = lib().rmb_greedy(ctypes.byref(mdp.desc), ctypes.byref(o), _ptr(V), _ptr(TV), _ptr(pi), _ptr(qgap),
                           _ptr(ws), ws.numel(), ctypes.byref(s) if s is not None else None, _stream_handle(stream))
     return _finish(st, s, "rmb_greedy", allow=(RMB_OK,)) if check else (st, s.as_dict() if s is not None else None)
+
+
+def rmb_vi_noalloc(mdp: DeviceMDP, opts: Opts, V, pi=None, qgap=None, stats: bool = True, stream=None,
+                   check: bool = True):
+    """MB-VI in place on V using the library's fixed scratch array instead of a workspace.
+
+    For callers that cannot allocate device memory (see rmb.h): no workspace argument, problems
+    needing more than RMB_NOALLOC_SCRATCH_BYTES of scratch are rejected (RMB_ERR_TOO_LARGE), and
+    calls that overlap on the GPU race on the shared array.
+    """
+    import torch
+    _check(V, torch.float32, mdp.n, "V")
+    _check(pi, torch.int32, mdp.n, "pi")
+    _check(qgap, torch.float32, mdp.n, "qgap")
+    f = lib().rmb_vi_noalloc
+    f.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.POINTER(rmb_opts), ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.POINTER(rmb_stats), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    o = opts.desc()
+    s = rmb_stats() if stats else None
+    st = f(ctypes.byref(mdp.desc), ctypes.byref(o), _ptr(V), _ptr(pi), _ptr(qgap),
+           ctypes.byref(s) if s is not None else None, _stream_handle(stream))
+    return _finish(st, s, "rmb_vi_noalloc") if check else (st, s.as_dict() if s is not None else None)
 
 
 def rmb_permutation(n: int, seed: int, sweep: int, out=None, stream=None):

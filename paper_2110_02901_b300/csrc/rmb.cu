@@ -1120,6 +1120,26 @@ int solve(const Call& q)
     return q.stats->status;
 }
 
+// Fixed scratch of rmb_vi_noalloc: a file-scope device array, one per GPU that loads the library.
+// In host code its name is only a host-side stand-in, never a device address: the address is
+// looked up once per device with cudaGetSymbolAddress (with that device current) and cached.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RMB_NOALLOC_SCRATCH_BYTES];
+void* g_noalloc_ptr[64];
+
+int noalloc_scratch(void** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return RMB_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RMB_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return RMB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1208,8 +1228,36 @@ const char* rmb_status_string(int status)
     case RMB_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case RMB_ERR_UNSUPPORTED: return "unsupported size or layout";
     case RMB_ERR_NONFINITE: return "non-finite value";
+    case RMB_ERR_TOO_LARGE: return "problem needs more scratch than the fixed no-allocation array holds";
     default: return "unknown status";
     }
+}
+
+int rmb_vi_noalloc(const rmb_mdp* mdp, const rmb_opts* opts, float* V_inout, int32_t* pi_out, float* qgap_out,
+                   rmb_stats* stats, void* stream)
+{
+    int st = check_mdp(mdp);
+    if (st) return st;
+    if (!opts) return RMB_ERR_ARG;
+    const size_t need = rmb_workspace_bytes(mdp, opts);
+    if (need == 0) return RMB_ERR_ARG;
+    if (need > RMB_NOALLOC_SCRATCH_BYTES) return RMB_ERR_TOO_LARGE;
+    void* ws = nullptr;
+    if ((st = noalloc_scratch(&ws))) return st;
+    st = rmb_vi(mdp, opts, V_inout, pi_out, qgap_out, ws, RMB_NOALLOC_SCRATCH_BYTES, nullptr, stream);
+    if (st != RMB_OK || !stats) return st;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return RMB_ERR_CUDA;
+    Ctrl h;
+    if (cudaMemcpy(&h, ws, sizeof(Ctrl), cudaMemcpyDeviceToHost) != cudaSuccess) return RMB_ERR_CUDA;
+    std::memset(stats, 0, sizeof(rmb_stats));
+    stats->sweeps = h.sweeps;
+    stats->iters = h.iters;
+    stats->barriers = h.barriers;
+    stats->residual = h.residual;
+    stats->v_shift = h.mu;
+    stats->status = h.status != 0 ? h.status : h.error;
+    stats->path = -1;
+    return stats->status;
 }
 
 uint64_t rmb_kernel_launches(void) { return g_launches.load(); }
