@@ -219,6 +219,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--ref-sweeps", type=int, default=3, help="reference arm: oracle sweeps per step")
     ap.add_argument("--n-log2", type=int, default=20, help="states = 2^n_log2 (profiling of smaller cases)")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="SWEEPS",
+                    help="profiling mode: one MB-VI solve of exactly SWEEPS sweeps (no bench line)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -246,6 +248,15 @@ def main():
     pi = torch.empty(n, dtype=torch.int32, device=dev)
     gap = torch.empty(n, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+
+    if args.profile_case:
+        po = rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=args.profile_case, validate=False)
+        st = rmb.rmb_vi(dm, po, V, pi, gap, ws=rmb.workspace(dm, po, device=dev), stream=stream)
+        gb = (st["sweeps"] + 1) * sweep_bytes(n, M_ACTIONS, K_SUCC) / 1e9
+        print(json.dumps({"profile_case": True, "n": n, "b": b, "sweeps": st["sweeps"], "ms": st["ms"],
+                          "p_stream_gb": gb, "gbs": gb / (st["ms"] / 1e3), "path": st["path"],
+                          "grid_ctas": st["grid_ctas"]}), flush=True)
+        return 0
 
     def solve():
         V.zero_()
