@@ -60,6 +60,9 @@ struct KP {
     double eps;
     uint32_t seed_lo, seed_hi, h;
     int lps_all, lps_one;   // CSR: lanes sharing one state (all actions / one row)
+    int nc_all, nc_one;     // CSR vectorised: float4 chunks per lane per state (0 = general loop)
+    int k4_log2;            // CSR vectorised: log2(k/4)
+    int32_t* perm_buf;      // non-null when a sweep has >= 4 batches: sigma of the coming sweep
     int stage;              // dense: floats of V staged per chunk
     // buffers
     const float* Vin;
@@ -109,8 +112,10 @@ __device__ __forceinline__ Best shfl_xor_best(Best v, int off)
 
 __device__ __forceinline__ float gather(const float* __restrict__ A, int j, uint32_t nm1)
 {
-    // clamp keeps an unvalidated bad index inside the buffer (validation reports it)
-    return ld_l2(A + min((uint32_t)j, nm1));
+    // clamp keeps an unvalidated bad index inside the buffer (validation reports it).  The read
+    // buffer does not change within a batch, and plain L1-cached loads issued after the grid-wide
+    // barrier's acquire observe every value released before it, so the gathers may hit in L1.
+    return __ldca(A + min((uint32_t)j, nm1));
 }
 
 // Q-factors of one state on the vectorised CSR path (every row has k entries, k % 4 == 0).
@@ -257,7 +262,7 @@ __device__ void csr_batch(const KP& p, int lps, const float* __restrict__ A, flo
         // each lane resolves the state of one (group, step) pair of the next 32/spw steps
         const int my_pos = first + (lane % spw) + (j0 + lane / spw) * U;
         int my_state = -1;
-        if (my_pos < len) my_state = K ? (int)perm_at((uint32_t)(pos0 + my_pos), *K, perm_ok) : pos0 + my_pos;
+        if (my_pos < len) my_state = K ? state_at((uint32_t)(pos0 + my_pos), *K, perm_ok) : pos0 + my_pos;
         for (int jj = 0; jj < 32 / spw; ++jj) {
             const int j = j0 + jj;
             if (first + j * U >= len) break;
@@ -271,6 +276,182 @@ __device__ void csr_batch(const KP& p, int lps, const float* __restrict__ A, flo
                                : csr_gen_state<ARG>(p, ss, pi_s, act, A, lane);
             if (act && lane_g == 0) state_epilogue<KIND>(p, r, s, first + g + j * U, A, B, Sout, Wout, C, acc);
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Fast CSR path (k/4 <= lanes per state, at most 4 float4 chunks per lane and state).  Every lane
+// loads all its chunks of a state at once, and the next state's rows are prefetched while the
+// current state's successor gathers resolve.  The first state of the next batch is prefetched
+// between the arrival at and the wait on the grid-wide barrier (its rows and position in the
+// permutation do not depend on the values being written), so small batches do not pay the
+// permutation and HBM latency after every barrier.
+// ------------------------------------------------------------------------------------------------
+template <int NC>
+struct StateRegs {
+    float4 p[NC];
+    int4 c[NC];
+    float cost[NC];
+};
+
+template <int NC>
+struct Carry {
+    StateRegs<NC> R;
+    int block_states;   // this lane's state for (group, step) of the first permutation block
+    int s;              // the group's first state (-1 = none)
+    bool valid;
+};
+
+template <int KIND, int NC>
+__device__ __forceinline__ void fast_load(const KP& p, int s, bool act, int lps, int lane_g, StateRegs<NC>& R)
+{
+    int pi_s = -1;
+    if (KIND == K_POLICY && act)
+        pi_s = (int)min((uint32_t)ld_l2(p.pi_in ? p.pi_in + s : p.pi + s), (uint32_t)(p.m - 1));
+    const int total = (KIND == K_POLICY ? 1 : p.m) << p.k4_log2;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int ci = c * lps + lane_g;
+        const bool v = act && ci < total;
+        const int row = ci >> p.k4_log2;
+        const int ch = ci - (row << p.k4_log2);
+        const int a = KIND == K_POLICY ? pi_s : row;
+        const int64_t r = (int64_t)s * p.m + a;
+        if (v) {
+            R.p[c] = __ldcs(reinterpret_cast<const float4*>(p.prob + r * p.k) + ch);
+            R.c[c] = __ldcs(reinterpret_cast<const int4*>(p.col + r * p.k) + ch);
+            R.cost[c] = __ldg(p.cost + r);
+        } else {
+            R.p[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            R.c[c] = make_int4(0, 0, 0, 0);
+            R.cost[c] = kInf;
+        }
+    }
+}
+
+// min (and, with ARG, the lowest arg-min and the second smallest value) over the state's rows of
+// c + gamma * sum p * A[col]; every lane of the group gets the result
+template <bool ARG, int NC>
+__device__ __forceinline__ Best fast_eval(const KP& p, const StateRegs<NC>& R, const float* __restrict__ A, int lps,
+                                          int lane_g)
+{
+    const uint32_t nm1 = (uint32_t)(p.n - 1);
+    float part[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float g0 = gather(A, R.c[c].x, nm1), g1 = gather(A, R.c[c].y, nm1);
+        const float g2 = gather(A, R.c[c].z, nm1), g3 = gather(A, R.c[c].w, nm1);
+        part[c] = fmaf(R.p[c].x, g0, fmaf(R.p[c].y, g1, fmaf(R.p[c].z, g2, R.p[c].w * g3)));
+    }
+    const int k4 = 1 << p.k4_log2;
+    for (int off = 1; off < k4; off <<= 1) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) part[c] += __shfl_xor_sync(0xffffffffu, part[c], off);
+    }
+    Best b = {kInf, 0x7fffffff, kInf};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const float q = R.cost[c] == kInf ? kInf : fmaf(p.gamma, part[c], R.cost[c]);
+        if (ARG) b = better(b, Best{q, (c * lps + lane_g) >> p.k4_log2, kInf});
+        else b.q = fminf(b.q, q);
+    }
+    for (int off = k4; off < lps; off <<= 1) {
+        if (ARG) b = better(b, shfl_xor_best<true>(b, off));
+        else b.q = fminf(b.q, __shfl_xor_sync(0xffffffffu, b.q, off));
+    }
+    return b;
+}
+
+struct FastGeom {
+    int lane, spw, per_block, g, lane_g, U, first, my_off, my_step;
+    __device__ FastGeom(int lps)
+    {
+        lane = threadIdx.x & 31;
+        const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+        const int nwarps = (gridDim.x * blockDim.x) >> 5;
+        spw = 32 / lps;
+        per_block = 32 / spw;          // steps covered by one permutation evaluation per lane
+        g = lane / lps;
+        lane_g = lane - g * lps;
+        U = nwarps * spw;
+        first = warp * spw;
+        my_off = first + (lane % spw);
+        my_step = lane / spw;
+    }
+    __device__ int resolve(int j0, int pos0, int len, const PermKey* K, bool* ok) const
+    {
+        const int pos = my_off + (j0 + my_step) * U;
+        if (pos >= len) return -1;
+        return K ? state_at((uint32_t)(pos0 + pos), *K, ok) : pos0 + pos;
+    }
+};
+
+// resolve and load this warp's first state of a batch ahead of time
+template <int KIND, int NC>
+__device__ __forceinline__ void fast_prefetch_first(const KP& p, int lps, int pos0, int len, const PermKey* K,
+                                                    Carry<NC>& carry, bool* perm_ok)
+{
+    const FastGeom G(lps);
+    carry.valid = false;
+    if (G.first >= len) return;
+    carry.block_states = G.resolve(0, pos0, len, K, perm_ok);
+    carry.s = __shfl_sync(0xffffffffu, carry.block_states, G.g);
+    fast_load<KIND, NC>(p, carry.s < 0 ? 0 : carry.s, carry.s >= 0, lps, G.lane_g, carry.R);
+    carry.valid = true;
+}
+
+template <int KIND, int NC>
+__device__ void csr_batch_fast(const KP& p, int lps, const float* __restrict__ A, float* B, int pos0, int len,
+                               const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc, bool* perm_ok,
+                               Carry<NC>& carry)
+{
+    constexpr bool ARG = (KIND == K_GREEDY);
+    constexpr int LK = (KIND == K_POLICY) ? K_POLICY : K_MIN;   // which rows to load
+    const FastGeom G(lps);
+    if (G.first >= len) { carry.valid = false; return; }
+    int block_states, s_cur;
+    StateRegs<NC> cur, nxt;
+    if (carry.valid) {
+        block_states = carry.block_states;
+        s_cur = carry.s;
+        cur = carry.R;
+    } else {
+        block_states = G.resolve(0, pos0, len, K, perm_ok);
+        s_cur = __shfl_sync(0xffffffffu, block_states, G.g);
+        fast_load<LK, NC>(p, s_cur < 0 ? 0 : s_cur, s_cur >= 0, lps, G.lane_g, cur);
+    }
+    carry.valid = false;
+    for (int j = 0; G.first + j * G.U < len; ++j) {
+        const int jn = j + 1;
+        int s_nxt = -1;
+        if (G.first + jn * G.U < len) {
+            if (jn % G.per_block == 0) block_states = G.resolve(jn, pos0, len, K, perm_ok);
+            s_nxt = __shfl_sync(0xffffffffu, block_states, (jn % G.per_block) * G.spw + G.g);
+        }
+        fast_load<LK, NC>(p, s_nxt < 0 ? 0 : s_nxt, s_nxt >= 0, lps, G.lane_g, nxt);
+        const bool lead = s_cur >= 0 && G.lane_g == 0;
+        const float old = lead ? ld_l2(A + s_cur) : 0.f;
+        const Best r = fast_eval<ARG, NC>(p, cur, A, lps, G.lane_g);
+        if (lead) {
+            const float v = new_value(r.q, C);
+            if (v != v) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
+            acc.dmax = fmaxf(acc.dmax, fabsf(v - old));
+            if (KIND == K_GREEDY) {
+                if (p.pi) st_l2(p.pi + s_cur, r.a);
+                if (p.qgap) p.qgap[s_cur] = r.q2 - r.q;
+                if (p.TVout) p.TVout[s_cur] = (float)((double)r.q + p.gamma_d * C.mu);
+                if (p.Vout) p.Vout[s_cur] = (float)(C.mu + (double)old);
+            } else {
+                acc.vlo = fminf(acc.vlo, v);
+                acc.vhi = fmaxf(acc.vhi, v);
+                const int i = G.first + G.g + j * G.U;
+                st_l2(Sout + i, s_cur);
+                st_l2(Wout + i, v);
+                st_l2(B + s_cur, v);
+            }
+        }
+        cur = nxt;
+        s_cur = s_nxt;
     }
 }
 
@@ -417,7 +598,7 @@ __device__ bool dense_batch(const KP& p, DenseSmem& sm, float* stage, const floa
         if (threadIdx.x < 32) {
             const int pos = (int)blockIdx.x + (j0 + (int)threadIdx.x) * G;
             int st = -1;
-            if (pos < len) st = K ? (int)perm_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
+            if (pos < len) st = K ? state_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
             sm.perm[threadIdx.x] = st;
         }
         __syncthreads();
@@ -486,7 +667,7 @@ __device__ __forceinline__ void read_slot(Ctrl* c, int slot, RedSmem& rs, float&
     __syncthreads();
 }
 
-template <int PATH>
+template <int PATH, int NCA = 0, int NCO = 0>
 struct Runner {
     const KP& p;
     Ctrl* c;
@@ -503,19 +684,36 @@ struct Runner {
 
     __device__ Runner(const KP& kp, RedSmem& r, DenseSmem* d, float* st)
         : p(kp), c(kp.ctrl), target(0), barriers(0), stall(false), cur(0), red_epoch(0), rs(r), dsm(d),
-          stage(st), perm_ok(true) {}
+          stage(st), perm_ok(true)
+    {
+        carry_a.valid = false;
+        carry_o.valid = false;
+    }
 
     __device__ bool sync(int site)
+    {
+        arrive();
+        return wait(site);
+    }
+    // split grid-wide barrier: work between arrive() and wait() must not read what other CTAs
+    // write before their arrival
+    __device__ void arrive()
     {
         const bool skip = stall;
         stall = false;
         if (!perm_ok) atomicCAS(&c->error, 0, RMB_ERR_UNSUPPORTED);
         ++barriers;
-        return grid_wait(c, target, p.timeout_ns, skip, site);
+        grid_arrive(c, target, skip);
     }
+    __device__ bool wait(int site) { return grid_wait_arrived(c, target, p.timeout_ns, site); }
 
     __device__ size_t gtid() const { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
     __device__ size_t gthreads() const { return (size_t)gridDim.x * blockDim.x; }
+
+    static constexpr int NCA_ = NCA > 0 ? NCA : 1;
+    static constexpr int NCO_ = NCO > 0 ? NCO : 1;
+    Carry<NCA_> carry_a;    // prefetched first state of the next min-over-actions batch
+    Carry<NCO_> carry_o;    // ... of the next policy-row batch
 
     template <int KIND>
     __device__ bool batch(const float* A, float* B, int pos0, int len, const PermKey* K, int32_t* So, float* Wo,
@@ -527,9 +725,28 @@ struct Runner {
             return dense_batch<KIND, false>(p, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
         } else {
             const int lps = (KIND == K_POLICY) ? p.lps_one : p.lps_all;
+            if (PATH == PATH_CSR_VEC && KIND == K_POLICY && NCO > 0) {
+                csr_batch_fast<K_POLICY, NCO_>(p, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok, carry_o);
+                return true;
+            }
+            if (PATH == PATH_CSR_VEC && KIND != K_POLICY && NCA > 0) {
+                carry_a.valid = carry_a.valid && KIND == K_MIN;
+                csr_batch_fast<KIND == K_GREEDY ? K_GREEDY : K_MIN, NCA_>(p, lps, A, B, pos0, len, K, So, Wo, C, acc,
+                                                                         &perm_ok, carry_a);
+                return true;
+            }
             csr_batch<KIND, PATH == PATH_CSR_VEC>(p, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
             return true;
         }
+    }
+
+    // between arrive() and wait(): load the first state of the next batch of the same sweep
+    template <int KIND>
+    __device__ void prefetch_next(int pos0, int len, const PermKey* K)
+    {
+        if (PATH != PATH_CSR_VEC) return;
+        if (KIND == K_POLICY && NCO > 0) fast_prefetch_first<K_POLICY, NCO_>(p, p.lps_one, pos0, len, K, carry_o, &perm_ok);
+        if (KIND == K_MIN && NCA > 0) fast_prefetch_first<K_MIN, NCA_>(p, p.lps_all, pos0, len, K, carry_a, &perm_ok);
     }
 
     __device__ void copy_batch(const int32_t* S, const float* Wv, int len, float* B)
@@ -549,10 +766,7 @@ struct Runner {
         return mid;
     }
 
-    // One sweep of B_b (KIND K_MIN) or B_{pi,b} (K_POLICY).  Returns false on failure; sets stop.
-    // can_stop: VI / evaluation (may end after this sweep); MPI evaluation sweeps always complete
-    template <int KIND>
-    __device__ bool sweep(long long k, long long j, bool can_stop, bool is_last, bool& stop, float& delta)
+    __device__ PermKey key_for(long long k) const
     {
         PermKey K;
         K.n = (uint32_t)p.n;
@@ -562,6 +776,27 @@ struct Runner {
         K.k1 = p.seed_hi;
         K.s_lo = (uint32_t)(unsigned long long)k;
         K.s_hi = (uint32_t)((unsigned long long)k >> 32);
+        K.buf = nullptr;
+        return K;
+    }
+
+    // sigma of sweep k for every position, by the whole grid, into the permutation buffer (done in a
+    // phase that ends with a grid-wide barrier, before sweep k starts)
+    __device__ void compute_perm(long long k)
+    {
+        if (!p.perm_buf) return;
+        const PermKey K = key_for(k);
+        for (size_t i = gtid(); i < (size_t)p.n; i += gthreads())
+            st_l2(p.perm_buf + i, (int)perm_at((uint32_t)i, K, &perm_ok));
+    }
+
+    // One sweep of B_b (KIND K_MIN) or B_{pi,b} (K_POLICY).  Returns false on failure; sets stop.
+    // can_stop: VI / evaluation (may end after this sweep); MPI evaluation sweeps always complete
+    template <int KIND>
+    __device__ bool sweep(long long k, long long j, bool can_stop, bool is_last, bool& stop, float& delta)
+    {
+        PermKey K = key_for(k);
+        K.buf = p.perm_buf;
         const int slot = red_epoch % 3;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             const int nxt = (red_epoch + 1) % 3;
@@ -574,11 +809,14 @@ struct Runner {
         for (int t = 0; t < p.T; ++t) {
             float* A = p.d[(cur + t) & 1];
             float* B = p.d[(cur + t + 1) & 1];
-            if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B);
             const int len = (t == p.T - 1) ? p.last_len : p.b;
             if (!batch<KIND>(A, B, t * p.b, len, &K, p.S[t & 1], p.W[t & 1], acc)) return false;
+            // B must also receive batch t-1's new values before the next batch reads it
+            if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B);
             if (t == p.T - 1) publish(c, slot, acc, rs);
-            if (!sync(10 + (t & 1))) return false;
+            arrive();
+            if (t + 1 < p.T) prefetch_next<KIND>((t + 1) * p.b, (t + 2 == p.T) ? p.last_len : p.b, &K);
+            if (!wait(10 + (t & 1))) return false;
         }
         float lo, hi;
         read_slot(c, slot, rs, delta, lo, hi);
@@ -601,16 +839,20 @@ struct Runner {
                 st_l2(O + i, v);
             }
             C = make_centre(C.mu + (double)shift, p.gamma_d);
+            compute_perm(k + 1);
             if (!sync(20)) return false;
         } else if (p.T >= 2) {
             copy_batch(p.S[(p.T - 1) & 1], p.W[(p.T - 1) & 1], p.last_len, p.d[cur ^ 1]);
+            compute_perm(k + 1);
             if (!sync(21)) return false;
         }
         return true;
     }
 
     // Full Bellman pass at the current values: greedy policy, Q-gap, TV, ||TV - V||_inf, V out.
-    __device__ bool greedy_pass(float& resid)
+    // next_k >= 0: also prepare the permutation of sweep next_k (MPI: the evaluation sweep that may
+    // follow).
+    __device__ bool greedy_pass(float& resid, long long next_k = -1)
     {
         const int slot = red_epoch % 3;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -622,7 +864,9 @@ struct Runner {
         ++red_epoch;
         Acc acc = {0.f, kInf, -kInf};
         const float* A = p.d[cur];
+        carry_a.valid = false;
         if (!batch<K_GREEDY>(A, nullptr, 0, p.n, nullptr, nullptr, nullptr, acc)) return false;
+        if (next_k >= 0) compute_perm(next_k);
         publish(c, slot, acc, rs);
         if (!sync(30)) return false;
         float lo, hi;
@@ -671,6 +915,7 @@ struct Runner {
             st_l2(p.d[0] + i, v);
             st_l2(p.d[1] + i, v);
         }
+        if (p.mode == MODE_VI || p.mode == MODE_EVAL) compute_perm(p.start_sweep);
         if (!sync(2)) return finish(false, 0, 0, 0.0);
         cur = 0;
 
@@ -709,7 +954,7 @@ struct Runner {
         // MODE_MPI (Alg. 1): improvement pass, stop test, K evaluation sweeps of B_{pi,b}
         for (;;) {
             float r;
-            if (!greedy_pass(r)) return finish(false, sweeps, iters, residual);   // also writes V
+            if (!greedy_pass(r, p.start_sweep + sweeps)) return finish(false, sweeps, iters, residual);   // also writes V
             residual = (double)r;
             if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace) p.trace[iters] = residual;
             ++iters;
@@ -741,10 +986,13 @@ struct Runner {
     }
 };
 
-__global__ void __launch_bounds__(kCsrThreads, 2) rmb_csr_vec_kernel(KP p)
+// CSR rows with k % 4 == 0: NCA / NCO = float4 chunks per lane in the min-over-actions sweeps and in
+// the policy-row sweeps (0 = the general row loop).
+template <int NCA, int NCO>
+__global__ void __launch_bounds__(kCsrThreads, 1) rmb_csr_vec_kernel(KP p)
 {
     __shared__ RedSmem rs;
-    Runner<PATH_CSR_VEC> R(p, rs, nullptr, nullptr);
+    Runner<PATH_CSR_VEC, NCA, NCO> R(p, rs, nullptr, nullptr);
     R.run();
 }
 
@@ -770,7 +1018,7 @@ __global__ void __launch_bounds__(kDenseThreads, 3) rmb_dense_kernel(KP p)
 __global__ void rmb_perm_kernel(uint32_t n, uint32_t h, uint32_t k0, uint32_t k1, uint32_t s_lo, uint32_t s_hi,
                                 int32_t* out)
 {
-    PermKey K{n, h, (1u << h) - 1u, k0, k1, s_lo, s_hi};
+    PermKey K{n, h, (1u << h) - 1u, k0, k1, s_lo, s_hi, nullptr};
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
         bool ok = true;
         const uint32_t x = perm_at((uint32_t)p, K, &ok);
@@ -846,7 +1094,6 @@ std::atomic<uint64_t> g_launches{0};
 
 struct DevInfo {
     int sms = 0;
-    int occ_csr_vec = 0, occ_csr_gen = 0;
     bool init = false;
 };
 DevInfo g_dev[64];
@@ -860,10 +1107,6 @@ int dev_info(DevInfo** out)
     DevInfo& d = g_dev[dev];
     if (!d.init) {
         if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return RMB_ERR_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_csr_vec, rmb_csr_vec_kernel, kCsrThreads, 0) != cudaSuccess)
-            return RMB_ERR_CUDA;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_csr_gen, rmb_csr_gen_kernel, kCsrThreads, 0) != cudaSuccess)
-            return RMB_ERR_CUDA;
         d.init = true;
     }
     *out = &d;
@@ -873,8 +1116,12 @@ int dev_info(DevInfo** out)
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctrl, d0, d1, s0, s1, w0, w1, total;
+    size_t ctrl, d0, d1, s0, s1, w0, w1, pb, total;
+    bool perm_buf;
 };
+
+// A sweep with at least this many batches precomputes its permutation into the workspace.
+constexpr int64_t kPermBufMinBatches = 16;
 
 Layout layout(int64_t n, int64_t b)
 {
@@ -888,7 +1135,9 @@ Layout layout(int64_t n, int64_t b)
     L.s1 = L.s0 + bb;
     L.w0 = L.s1 + bb;
     L.w1 = L.w0 + bb;
-    L.total = L.w1 + bb;
+    L.pb = L.w1 + bb;
+    L.perm_buf = (n + b - 1) / b >= kPermBufMinBatches;
+    L.total = L.pb + (L.perm_buf ? nb : 0);
     return L;
 }
 
@@ -926,6 +1175,16 @@ bool csr_vec_ok(const rmb_mdp* M)
     if (!(pow2 || k4 % 32 == 0)) return false;
     if (((uintptr_t)M->prob & 15) || ((uintptr_t)M->col & 15)) return false;
     return true;
+}
+
+const void* csr_vec_kernel_for(int nca, int nco)
+{
+    const int a = (nca == 1 || nca == 2 || nca == 4) ? nca : 0;
+    const int o = nco == 1 ? 1 : 0;
+#define RMB_K(A_, O_) if (a == A_ && o == O_) return reinterpret_cast<const void*>(rmb_csr_vec_kernel<A_, O_>);
+    RMB_K(0, 0) RMB_K(1, 0) RMB_K(2, 0) RMB_K(4, 0) RMB_K(0, 1) RMB_K(1, 1) RMB_K(2, 1) RMB_K(4, 1)
+#undef RMB_K
+    return reinterpret_cast<const void*>(rmb_csr_vec_kernel<0, 0>);
 }
 
 int pow2ceil(int x)
@@ -1030,6 +1289,7 @@ int solve(const Call& q)
     p.S[1] = reinterpret_cast<int32_t*>(ws + L.s1);
     p.W[0] = reinterpret_cast<float*>(ws + L.w0);
     p.W[1] = reinterpret_cast<float*>(ws + L.w1);
+    p.perm_buf = (L.perm_buf && q.mode != MODE_GREEDY) ? reinterpret_cast<int32_t*>(ws + L.pb) : nullptr;
     p.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
     p.trace = q.mode == MODE_GREEDY ? nullptr : O->trace;
     p.timeout_ns = O->barrier_timeout_ns > 0 ? O->barrier_timeout_ns : 2000000000LL;
@@ -1046,6 +1306,17 @@ int solve(const Call& q)
         p.lps_one = cpr;
         int all = pow2ceil(cpr * p.m);
         p.lps_all = all > 32 ? 32 : all;
+        int lg = 0;
+        while ((1 << lg) < k4) ++lg;
+        p.k4_log2 = lg;
+        // fast path: a row's chunks fit in one lane group and a lane holds <= 4 chunks of a state
+        auto nc_of = [&](int rows, int lps) {
+            if (k4 > lps || (k4 & (k4 - 1))) return 0;
+            const int nc = (rows * k4 + lps - 1) / lps;
+            return (nc == 1 || nc == 2 || nc == 4) ? nc : (nc == 3 ? 4 : 0);
+        };
+        p.nc_all = nc_of(p.m, p.lps_all);
+        p.nc_one = nc_of(1, p.lps_one) == 1 ? 1 : 0;
     } else {
         p.lps_one = 32;
         p.lps_all = 32;
@@ -1071,10 +1342,14 @@ int solve(const Call& q)
             return RMB_ERR_CUDA;
         per_sm = occ < 2 ? occ : 2;
     } else {
-        fn = path == PATH_CSR_VEC ? reinterpret_cast<const void*>(rmb_csr_vec_kernel)
+        fn = path == PATH_CSR_VEC ? csr_vec_kernel_for(p.nc_all, p.nc_one)
                                   : reinterpret_cast<const void*>(rmb_csr_gen_kernel);
         threads = kCsrThreads;
-        const int occ = path == PATH_CSR_VEC ? D->occ_csr_vec : D->occ_csr_gen;
+        // the CSR kernels use almost no shared memory: give the unified L1 as much as possible for
+        // the successor gathers
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess) return RMB_ERR_CUDA;
         per_sm = occ < 4 ? occ : 4;
     }
     if (per_sm < 1) return RMB_ERR_CUDA;

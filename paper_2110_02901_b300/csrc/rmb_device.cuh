@@ -36,6 +36,7 @@ __device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t
 // to [0,n) within (4^h - n + 1) steps; *ok is cleared if that bound is ever exceeded.
 struct PermKey {
     uint32_t n, h, mask, k0, k1, s_lo, s_hi;
+    const int32_t* buf;   // non-null: sigma of this sweep is precomputed here (buf[p] = sigma(p))
 };
 
 __device__ __forceinline__ uint32_t feistel8(uint32_t x, const PermKey& K)
@@ -61,6 +62,13 @@ __device__ __forceinline__ uint32_t perm_at(uint32_t p, const PermKey& K, bool* 
         if (++steps > limit) { *ok = false; return 0; }
     } while (x >= K.n);
     return x;
+}
+
+// sigma(p) from the precomputed buffer when there is one, else evaluated here
+__device__ __forceinline__ int state_at(uint32_t p, const PermKey& K, bool* ok)
+{
+    if (K.buf) return __ldcg(K.buf + p);
+    return (int)perm_at(p, K, ok);
 }
 
 __host__ __device__ inline uint32_t perm_half_bits(int64_t n)
@@ -132,18 +140,24 @@ struct Ctrl {
     int status, pad;
 };
 
-// Bounded grid-wide wait.  Thread 0 of every CTA publishes its arrival with a release add and
-// spins on an acquire load; it gives up after timeout_ns (or as soon as another CTA reports an
-// error) and the call then returns false in every thread of the CTA.
-__device__ __forceinline__ bool grid_wait(Ctrl* c, unsigned long long& target, int64_t timeout_ns,
-                                          bool skip_arrive, int site)
+// Bounded grid-wide barrier, split in two: grid_arrive() publishes this CTA's arrival (thread 0,
+// release add after a CTA barrier and a fence), grid_wait_arrived() spins with acquire loads until
+// every CTA has arrived.  A wait gives up after timeout_ns, or as soon as another CTA reports an
+// error, and then returns false in every thread of the CTA.
+__device__ __forceinline__ void grid_arrive(Ctrl* c, unsigned long long& target, bool skip_arrive)
 {
-    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
         __threadfence();
         if (!skip_arrive) red_release_add_u64(&c->bar, 1ull);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait_arrived(Ctrl* c, unsigned long long target, int64_t timeout_ns, int site)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
         int ok = 1;
         const uint64_t t0 = globaltimer_ns();
         uint32_t spins = 0;

@@ -145,8 +145,11 @@ def test_workspace_size_formula(L):
     d = _fake_mdp(n=1000)
     o = _opts(b=64)
     nb = L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o))
-    # control block + two value buffers + two position caches + two value caches, 256-byte aligned
-    assert nb == 256 + 2 * 4096 + 4 * 256
+    # control block + two value buffers + two position caches + two value caches, 256-byte aligned,
+    # + the precomputed permutation when a sweep has >= 16 batches (here 16)
+    assert nb == 256 + 2 * 4096 + 4 * 256 + 4096
+    o.batch = 67            # 15 batches: evaluated on the fly
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 256 + 2 * 4096 + 4 * 512
     o.batch = 5000          # b > n means b = n
     assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 256 + 6 * 4096
     d.gamma = 2.0
