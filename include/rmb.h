@@ -93,6 +93,9 @@ typedef struct {
 /* Test-only fault injection: CTA 0 never arrives at the first grid-wide wait, so every wait runs
    out and the call must report RMB_ERR_BARRIER_TIMEOUT with the GPU context intact. */
 #define RMB_FLAG_INJECT_BARRIER_STALL 1
+/* Rows need not sum to 1 (used for the transposed chain of rmb_fixed_point_grad): values are kept
+   uncentred (mu = 0) and the sweeps run in plain float32. */
+#define RMB_FLAG_RAW_ROWS 2
 
 /* Results of a solve (filled only when a stats pointer is passed). */
 typedef struct {
@@ -203,6 +206,33 @@ int rmb_validate(const rmb_mdp *mdp, void *workspace, size_t workspace_bytes, vo
 #define RMB_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 int rmb_vi_noalloc(const rmb_mdp *mdp, const rmb_opts *opts, float *V_inout, int32_t *pi_out,
                    float *qgap_out, rmb_stats *stats, void *stream);
+
+/*
+ * P(.|s,a) = softmax of the row's logits over its k successors (RMB_CSR with k_uniform = k > 0):
+ * the parametrisation whose gradient rmb_fixed_point_grad returns.  logits, prob_out: [n*m*k], device.
+ */
+int rmb_softmax_rows(const rmb_mdp *mdp, const float *logits, float *prob_out, void *stream);
+
+/* Workspace bytes of rmb_fixed_point_grad (0 on invalid arguments or non-uniform CSR rows). */
+size_t rmb_fixed_point_grad_workspace_bytes(const rmb_mdp *mdp, const rmb_opts *opts);
+
+/*
+ * Gradient of L = w . V* with respect to the stage costs and the transition logits, through the
+ * Bellman equation (eq. (5)) at the greedy policy pi (implicit function theorem, valid away from
+ * action ties): V* = g_pi + gamma P_pi V*, so the adjoint lambda solves (I - gamma P_pi)^T lambda = w
+ * and
+ *   dL/dcost(s,a)    = lambda(s) [a = pi(s)],
+ *   dL/dlogit(s,a,t) = gamma lambda(s) [a = pi(s)] p_t (V*(j_t) - sum_u p_u V*(j_u)).
+ * lambda is computed by mini-batch sweeps (b = opts.batch, the permutation of opts.seed) of
+ * lambda <- w + gamma P_pi^T lambda on the transposed greedy chain, built on the device (rows sorted
+ * by predecessor, so the result is deterministic), starting from lambda = w, until the sup-norm
+ * change of a sweep is <= opts.eps or opts.max_sweeps.  RMB_CSR with k_uniform > 0 only.
+ *   pi [n] (the greedy policy of V*), V [n] (= V*), w [n]: device inputs.
+ *   lambda_out [n]; grad_cost [n*m] or NULL; grad_logits [n*m*k] or NULL: device outputs.
+ */
+int rmb_fixed_point_grad(const rmb_mdp *mdp, const int32_t *pi, const float *V, const float *w,
+                         const rmb_opts *opts, float *lambda_out, float *grad_cost, float *grad_logits,
+                         void *workspace, size_t workspace_bytes, rmb_stats *stats, void *stream);
 
 /* Static text for a status code. */
 const char *rmb_status_string(int status);

@@ -50,11 +50,9 @@ def policy_value(mdp, pi, method: str = "auto"):
     a = float(mdp.gamma)
     if sp.issparse(Pm):
         A = (sp.identity(n, format="csr") - a * Pm).tocsc()
-        if method == "gmres" or (method == "auto" and n > 20000):
-            x, info = spla.gmres(A, g, rtol=1e-14, atol=0.0, restart=200, maxiter=10000)
-            if info != 0:
-                raise RuntimeError(f"gmres did not converge (info={info})")
-            return x
+        # sparse LU fills in badly on random successor structure: GMRES beyond small n
+        if method == "gmres" or (method == "auto" and n > 1000):
+            return _gmres(A, g)
         return spla.spsolve(A, g)
     A = np.eye(n) - a * Pm
     return np.linalg.solve(A, g)
@@ -112,3 +110,66 @@ def policy_iteration(mdp, max_iters: int = 200):
             return J, pi, float(np.max(np.abs(TJ - J)))
         pi = new_pi
     raise RuntimeError("policy iteration did not terminate")
+
+
+def softmax_rows(logits, row_ptr):
+    """P(.|s,a) = softmax of the row's logits over its successors, in FP64."""
+    z = np.asarray(logits, dtype=np.float64)
+    rows = len(row_ptr) - 1
+    if rows and len(z) % rows == 0 and np.array_equal(row_ptr, np.arange(rows + 1) * (len(z) // rows)):
+        zz = z.reshape(rows, -1)
+        e = np.exp(zz - zz.max(axis=1, keepdims=True))
+        return (e / e.sum(axis=1, keepdims=True)).reshape(-1)
+    out = np.empty_like(z)
+    for r in range(rows):
+        a, b = int(row_ptr[r]), int(row_ptr[r + 1])
+        e = np.exp(z[a:b] - z[a:b].max())
+        out[a:b] = e / e.sum()
+    return out
+
+
+def fixed_point_gradient(mdp, w, jstar=None, pistar=None):
+    """Gradient of L = w . J* (implicit function theorem on the Bellman equation, eq. (5), at a policy
+    mu* with no ties):  J* = g_mu + alpha P_mu J*  =>  lambda solves (I - alpha P_mu)^T lambda = w,
+      dL/dg(s,a)   = lambda(s) [a = mu(s)],
+      dL/dz(s,a,t) = alpha lambda(s) [a = mu(s)] p_t (J*(j_t) - sum_u p_u J*(j_u))   (p = softmax(z)).
+    Returns (lambda, dL/dcost [n*m], dL/dlogits [nnz] (CSR only), J*, mu*)."""
+    if jstar is None or pistar is None:
+        jstar, pistar, _ = policy_iteration(mdp)
+    Pm, _ = policy_matrix(mdp, pistar)
+    n = mdp.n
+    w = np.asarray(w, dtype=np.float64)
+    if sp.issparse(Pm):
+        A = (sp.identity(n, format="csr") - mdp.gamma * Pm).T.tocsc()
+        lam = spla.spsolve(A, w) if n <= 1000 else _gmres(A, w)
+    else:
+        lam = np.linalg.solve((np.eye(n) - mdp.gamma * Pm).T, w)
+    gc = np.zeros(n * mdp.m)
+    rows = np.arange(n, dtype=np.int64) * mdp.m + pistar
+    gc[rows] = lam
+    gz = None
+    if mdp.fmt == "csr":
+        gz = np.zeros(int(mdp.row_ptr[-1]))
+        p = mdp.prob.astype(np.float64)
+        k = int(mdp.row_ptr[-1]) // (n * mdp.m) if n * mdp.m else 0
+        if k and np.array_equal(mdp.row_ptr, np.arange(n * mdp.m + 1) * k):
+            idx = rows[:, None] * k + np.arange(k)[None, :]
+            pv = p[idx]
+            jv = jstar[mdp.col[idx]]
+            gz[idx] = mdp.gamma * lam[:, None] * pv * (jv - (pv * jv).sum(axis=1, keepdims=True))
+            return lam, gc, gz, jstar, pistar
+        for s in range(n):
+            r = int(rows[s])
+            a, b = int(mdp.row_ptr[r]), int(mdp.row_ptr[r + 1])
+            pv = p[a:b]
+            jv = jstar[mdp.col[a:b]]
+            gz[a:b] = mdp.gamma * lam[s] * pv * (jv - pv @ jv)
+    return lam, gc, gz, jstar, pistar
+
+
+def _gmres(A, b):
+    """GMRES to a 1e-14 relative residual; (I - alpha P) has inf-norm condition <= (1+alpha)/(1-alpha)."""
+    x, info = spla.gmres(A, b, rtol=1e-14, atol=0.0, restart=200, maxiter=10000)
+    if info != 0:
+        raise RuntimeError(f"gmres did not converge (info={info})")
+    return x

@@ -34,6 +34,7 @@ RMB_NOALLOC_SCRATCH_BYTES = 8 << 20
 RMB_DENSE = 0
 RMB_CSR = 1
 RMB_FLAG_INJECT_BARRIER_STALL = 1
+RMB_FLAG_RAW_ROWS = 2
 PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic"}
 
 
@@ -296,6 +297,57 @@ def rmb_vi_noalloc(mdp: DeviceMDP, opts: Opts, V, pi=None, qgap=None, stats: boo
     st = f(ctypes.byref(mdp.desc), ctypes.byref(o), _ptr(V), _ptr(pi), _ptr(qgap),
            ctypes.byref(s) if s is not None else None, _stream_handle(stream))
     return _finish(st, s, "rmb_vi_noalloc") if check else (st, s.as_dict() if s is not None else None)
+
+
+def rmb_softmax_rows(mdp: DeviceMDP, logits, prob_out, stream=None):
+    """prob_out = softmax of each (s,a) row of logits (CSR, uniform k)."""
+    import torch
+    nnz = mdp.n * mdp.m * mdp.k_uniform
+    _check(logits, torch.float32, nnz, "logits")
+    _check(prob_out, torch.float32, nnz, "prob_out")
+    f = lib().rmb_softmax_rows
+    f.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    st = f(ctypes.byref(mdp.desc), _ptr(logits), _ptr(prob_out), _stream_handle(stream))
+    if st != RMB_OK:
+        raise RmbError(st, "rmb_softmax_rows")
+    return prob_out
+
+
+def rmb_fixed_point_grad(mdp: DeviceMDP, pi, V, w, opts: Opts, lam=None, grad_cost=None, grad_logits=None,
+                         want_cost: bool = True, want_logits: bool = True, stats: bool = True, stream=None):
+    """Adjoint lambda of (I - gamma P_pi)^T lambda = w and the gradients of w . V* (see rmb.h).
+    Returns (lambda, dL/dcost, dL/dlogits, stats)."""
+    import torch
+    n, m, k = mdp.n, mdp.m, mdp.k_uniform
+    dev = V.device
+    lam = torch.empty(n, dtype=torch.float32, device=dev) if lam is None else lam
+    if want_cost and grad_cost is None:
+        grad_cost = torch.empty(n * m, dtype=torch.float32, device=dev)
+    if want_logits and grad_logits is None:
+        grad_logits = torch.empty(n * m * k, dtype=torch.float32, device=dev)
+    for t, dt, sz, nm in ((pi, torch.int32, n, "pi"), (V, torch.float32, n, "V"), (w, torch.float32, n, "w"),
+                          (lam, torch.float32, n, "lambda"), (grad_cost, torch.float32, n * m, "grad_cost"),
+                          (grad_logits, torch.float32, n * m * k, "grad_logits")):
+        _check(t, dt, sz, nm)
+    L = lib()
+    L.rmb_fixed_point_grad_workspace_bytes.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.POINTER(rmb_opts)]
+    L.rmb_fixed_point_grad_workspace_bytes.restype = ctypes.c_size_t
+    o = opts.desc()
+    nb = int(L.rmb_fixed_point_grad_workspace_bytes(ctypes.byref(mdp.desc), ctypes.byref(o)))
+    if nb == 0:
+        raise RmbError(RMB_ERR_ARG, "rmb_fixed_point_grad_workspace_bytes")
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    f = L.rmb_fixed_point_grad
+    f.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.POINTER(rmb_opts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_size_t, ctypes.POINTER(rmb_stats), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    s = rmb_stats() if stats else None
+    st = f(ctypes.byref(mdp.desc), _ptr(pi), _ptr(V), _ptr(w), ctypes.byref(o), _ptr(lam), _ptr(grad_cost),
+           _ptr(grad_logits), _ptr(ws), nb, ctypes.byref(s) if s is not None else None, _stream_handle(stream))
+    d = _finish(st, s, "rmb_fixed_point_grad")
+    return lam, grad_cost, grad_logits, d
 
 
 def rmb_permutation(n: int, seed: int, sweep: int, out=None, stream=None):

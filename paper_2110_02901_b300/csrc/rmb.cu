@@ -759,6 +759,7 @@ struct Runner {
     // other buffer gets the same, which also completes the end-of-sweep copy).
     __device__ float shift_for(float lo, float hi) const
     {
+        if (p.flags & RMB_FLAG_RAW_ROWS) return 0.f;
         const float mid = 0.5f * (lo + hi);
         const float spread = hi - lo;
         const float floor_ = 1e-6f * (float)(fabs(C.mu) + 1.0);
@@ -908,7 +909,8 @@ struct Runner {
         if (!sync(1)) return finish(false, 0, 0, 0.0);
         float dm, lo, hi;
         read_slot(c, 3, rs, dm, lo, hi);
-        const double mu0 = (double)(float)(0.5 * ((double)lo + (double)hi));
+        // rows that need not sum to 1 (RMB_FLAG_RAW_ROWS) keep the values uncentred: mu = 0
+        const double mu0 = (p.flags & RMB_FLAG_RAW_ROWS) ? 0.0 : (double)(float)(0.5 * ((double)lo + (double)hi));
         C = make_centre(mu0, p.gamma_d);
         for (size_t i = gtid(); i < (size_t)p.n; i += gthreads()) {
             const float v = (float)((double)p.Vin[i] - mu0);
@@ -1010,6 +1012,137 @@ __global__ void __launch_bounds__(kDenseThreads, 3) rmb_dense_kernel(KP p)
     extern __shared__ __align__(128) float stage[];
     Runner<PATH_DENSE> R(p, rs, &dsm, stage);
     R.run();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Differentiable fixed point (gradient of L = w . V* through the Bellman equation at the greedy
+// policy): row softmax, transposed greedy chain, gradient assembly.  The adjoint system
+// lambda = w + gamma P_pi^T lambda is solved by the persistent kernel's policy-row sweeps on the
+// transposed chain (one action per "state", rows = columns of P_pi).
+// ------------------------------------------------------------------------------------------------
+__global__ void rmb_softmax_kernel(int64_t rows, int k, const float* __restrict__ z, float* __restrict__ p)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < rows; r += nw) {
+        const float* zr = z + r * k;
+        float mx = -kInf;
+        for (int e = lane; e < k; e += 32) mx = fmaxf(mx, zr[e]);
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        float sum = 0.f;
+        for (int e = lane; e < k; e += 32) sum += expf(zr[e] - mx);
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        const float inv = 1.f / sum;
+        for (int e = lane; e < k; e += 32) p[r * k + e] = expf(zr[e] - mx) * inv;
+    }
+}
+
+// in-degree of every state in the greedy chain (rows r = s*m + pi(s), k entries each)
+__global__ void rmb_tr_count_kernel(int n, int m, int k, const int32_t* __restrict__ pi, const int32_t* __restrict__ col,
+                                    int32_t* __restrict__ cnt)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n * k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(e / k), t = (int)(e - (int64_t)s * k);
+        const int a = min((uint32_t)pi[s], (uint32_t)(m - 1));
+        const int j = col[((int64_t)s * m + a) * k + t];
+        atomicAdd(cnt + min((uint32_t)j, (uint32_t)(n - 1)), 1);
+    }
+}
+
+// exclusive scan of the counts into row_ptr (one CTA: runs once per gradient call)
+__global__ void rmb_tr_scan_kernel(int n, const int32_t* __restrict__ cnt, int64_t* __restrict__ row_ptr,
+                                   int32_t* __restrict__ cursor)
+{
+    __shared__ int64_t part[1024];
+    const int T = blockDim.x, t = threadIdx.x;
+    const int64_t per = ((int64_t)n + T - 1) / T;
+    const int64_t a = (int64_t)t * per, b = min((int64_t)n, a + per);
+    int64_t sum = 0;
+    for (int64_t i = a; i < b; ++i) sum += cnt[i];
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        int64_t run = 0;
+        for (int i = 0; i < T; ++i) {
+            const int64_t v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        row_ptr[n] = run;
+    }
+    __syncthreads();
+    int64_t run = part[t];
+    for (int64_t i = a; i < b; ++i) {
+        const int32_t c = cnt[i];   // cursor may alias cnt: read before writing
+        row_ptr[i] = run;
+        cursor[i] = (int32_t)run;
+        run += c;
+    }
+}
+
+__global__ void rmb_tr_scatter_kernel(int n, int m, int k, const int32_t* __restrict__ pi, const int32_t* __restrict__ col,
+                                      const float* __restrict__ prob, int32_t* __restrict__ cursor,
+                                      int32_t* __restrict__ colT, float* __restrict__ probT)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n * k;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int s = (int)(e / k), t = (int)(e - (int64_t)s * k);
+        const int a = min((uint32_t)pi[s], (uint32_t)(m - 1));
+        const int64_t src = ((int64_t)s * m + a) * k + t;
+        const int j = min((uint32_t)col[src], (uint32_t)(n - 1));
+        const int pos = atomicAdd(cursor + j, 1);
+        colT[pos] = s;
+        probT[pos] = prob[src];
+    }
+}
+
+// order each transposed row by source state, so sums run in a fixed order (deterministic results)
+__global__ void rmb_tr_sort_kernel(int n, const int64_t* __restrict__ row_ptr, int32_t* __restrict__ colT,
+                                   float* __restrict__ probT)
+{
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = row_ptr[j], b = row_ptr[j + 1];
+        for (int64_t i = a + 1; i < b; ++i) {
+            const int32_t c = colT[i];
+            const float pv = probT[i];
+            int64_t q = i - 1;
+            while (q >= a && colT[q] > c) {
+                colT[q + 1] = colT[q];
+                probT[q + 1] = probT[q];
+                --q;
+            }
+            colT[q + 1] = c;
+            probT[q + 1] = pv;
+        }
+    }
+}
+
+// dL/dcost(s, pi(s)) = lambda(s); dL/dz(s, pi(s), t) = gamma lambda(s) p_t (V(j_t) - sum_u p_u V(j_u))
+__global__ void rmb_grad_kernel(int n, int m, int k, float gamma, const int32_t* __restrict__ pi,
+                                const int32_t* __restrict__ col, const float* __restrict__ prob,
+                                const float* __restrict__ V, const float* __restrict__ lam,
+                                float* __restrict__ grad_cost, float* __restrict__ grad_z)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = warp; s < n; s += nw) {
+        const int a = min((uint32_t)pi[s], (uint32_t)(m - 1));
+        const int64_t r = s * m + a;
+        const float l = lam[s];
+        if (grad_cost && lane == 0) grad_cost[r] = l;
+        if (!grad_z) continue;
+        float mean = 0.f;
+        for (int t = lane; t < k; t += 32) mean = fmaf(prob[r * k + t], V[min((uint32_t)col[r * k + t], (uint32_t)(n - 1))], mean);
+        for (int off = 16; off > 0; off >>= 1) mean += __shfl_xor_sync(0xffffffffu, mean, off);
+        for (int t = lane; t < k; t += 32) {
+            const float pv = prob[r * k + t];
+            const float vj = V[min((uint32_t)col[r * k + t], (uint32_t)(n - 1))];
+            grad_z[r * k + t] = gamma * l * pv * (vj - mean);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1139,6 +1272,24 @@ Layout layout(int64_t n, int64_t b)
     L.perm_buf = (n + b - 1) / b >= kPermBufMinBatches;
     L.total = L.pb + (L.perm_buf ? nb : 0);
     return L;
+}
+
+struct GradLayout {
+    size_t rowT, colT, probT, cnt, zpi, eval, total;
+};
+
+GradLayout grad_layout(int64_t n, int64_t k, int64_t b)
+{
+    GradLayout G;
+    const int64_t nnzT = n * k;
+    G.rowT = 0;
+    G.colT = align_up((size_t)(n + 1) * 8, 256);
+    G.probT = G.colT + align_up((size_t)nnzT * 4, 256);
+    G.cnt = G.probT + align_up((size_t)nnzT * 4, 256);
+    G.zpi = G.cnt + align_up((size_t)n * 4, 256);
+    G.eval = G.zpi + align_up((size_t)n * 4, 256);
+    G.total = G.eval + layout(n, b).total;
+    return G;
 }
 
 int check_mdp(const rmb_mdp* M)
@@ -1489,6 +1640,97 @@ int rmb_validate(const rmb_mdp* mdp, void* workspace, size_t workspace_bytes, vo
     if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RMB_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
     return h;
+}
+
+int rmb_softmax_rows(const rmb_mdp* mdp, const float* logits, float* prob_out, void* stream)
+{
+    if (!mdp || !logits || !prob_out) return RMB_ERR_ARG;
+    if (mdp->format != RMB_CSR || mdp->k_uniform <= 0 || mdp->n < 1 || mdp->m < 1) return RMB_ERR_ARG;
+    DevInfo* D = nullptr;
+    int st = dev_info(&D);
+    if (st) return st;
+    const int64_t rows = mdp->n * (int64_t)mdp->m;
+    const int blocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)D->sms * 16);
+    rmb_softmax_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(rows, mdp->k_uniform, logits, prob_out);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
+}
+
+size_t rmb_fixed_point_grad_workspace_bytes(const rmb_mdp* mdp, const rmb_opts* opts)
+{
+    if (check_mdp(mdp) || mdp->format != RMB_CSR || mdp->k_uniform <= 0) return 0;
+    int64_t b = mdp->n;
+    if (opts && opts->batch >= 1) b = opts->batch > mdp->n ? mdp->n : opts->batch;
+    return grad_layout(mdp->n, mdp->k_uniform, b).total;
+}
+
+int rmb_fixed_point_grad(const rmb_mdp* mdp, const int32_t* pi, const float* V, const float* w, const rmb_opts* opts,
+                         float* lambda_out, float* grad_cost, float* grad_logits, void* workspace,
+                         size_t workspace_bytes, rmb_stats* stats, void* stream)
+{
+    int st = check_mdp(mdp);
+    if (st) return st;
+    if (mdp->format != RMB_CSR || mdp->k_uniform <= 0) return RMB_ERR_UNSUPPORTED;
+    if (mdp->n * (int64_t)mdp->k_uniform >= ((int64_t)1 << 31)) return RMB_ERR_UNSUPPORTED;
+    if (!pi || !V || !w || !lambda_out || !opts) return RMB_ERR_ARG;
+    if (opts->batch < 1 || opts->max_sweeps < 1 || !(opts->eps >= 0.0) || std::isinf(opts->eps)) return RMB_ERR_ARG;
+    const int64_t n = mdp->n;
+    const int k = mdp->k_uniform;
+    const int64_t b = opts->batch > n ? n : opts->batch;
+    const GradLayout G = grad_layout(n, k, b);
+    if (!workspace || ((uintptr_t)workspace & 255)) return RMB_ERR_WORKSPACE;
+    if (workspace_bytes < G.total) return RMB_ERR_WORKSPACE;
+    DevInfo* D = nullptr;
+    if ((st = dev_info(&D))) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(workspace);
+    int64_t* rowT = reinterpret_cast<int64_t*>(ws + G.rowT);
+    int32_t* colT = reinterpret_cast<int32_t*>(ws + G.colT);
+    float* probT = reinterpret_cast<float*>(ws + G.probT);
+    int32_t* cnt = reinterpret_cast<int32_t*>(ws + G.cnt);
+    int32_t* zpi = reinterpret_cast<int32_t*>(ws + G.zpi);
+    // 1. the transposed greedy chain: row j lists (i, p_ij(pi(i))) for every predecessor i
+    if (cudaMemsetAsync(cnt, 0, (size_t)n * 4, s) != cudaSuccess) return RMB_ERR_CUDA;
+    if (cudaMemsetAsync(zpi, 0, (size_t)n * 4, s) != cudaSuccess) return RMB_ERR_CUDA;
+    const int eb = (int)std::min<int64_t>((n * k + 255) / 256, (int64_t)D->sms * 16);
+    rmb_tr_count_kernel<<<eb, 256, 0, s>>>((int)n, mdp->m, k, pi, mdp->col, cnt);
+    rmb_tr_scan_kernel<<<1, 1024, 0, s>>>((int)n, cnt, rowT, cnt);
+    rmb_tr_scatter_kernel<<<eb, 256, 0, s>>>((int)n, mdp->m, k, pi, mdp->col, mdp->prob, cnt, colT, probT);
+    const int nb = (int)std::min<int64_t>((n + 255) / 256, (int64_t)D->sms * 8);
+    rmb_tr_sort_kernel<<<nb, 256, 0, s>>>((int)n, rowT, colT, probT);
+    g_launches += 4;
+    if (cudaGetLastError() != cudaSuccess) return RMB_ERR_CUDA;
+    // 2. adjoint sweeps lambda <- w + gamma P_pi^T lambda (mini-batch, one row per state), from lambda = w
+    rmb_mdp mt;
+    std::memset(&mt, 0, sizeof(mt));
+    mt.n = n;
+    mt.m = 1;
+    mt.format = RMB_CSR;
+    mt.row_ptr = rowT;
+    mt.col = colT;
+    mt.prob = probT;
+    mt.cost = w;
+    mt.gamma = mdp->gamma;
+    rmb_opts o2 = *opts;
+    o2.flags |= RMB_FLAG_RAW_ROWS;
+    o2.validate = 0;
+    if (cudaMemcpyAsync(lambda_out, w, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return RMB_ERR_CUDA;
+    Call q{MODE_EVAL, &mt, &o2, lambda_out, lambda_out, nullptr, nullptr, nullptr, zpi,
+           ws + G.eval, G.total - G.eval, stats, s};
+    st = solve(q);
+    if (st != RMB_OK && st != RMB_ERR_NOT_CONVERGED) return st;
+    // 3. gradients
+    if (grad_cost && cudaMemsetAsync(grad_cost, 0, (size_t)n * mdp->m * 4, s) != cudaSuccess) return RMB_ERR_CUDA;
+    if (grad_logits && cudaMemsetAsync(grad_logits, 0, (size_t)n * mdp->m * k * 4, s) != cudaSuccess) return RMB_ERR_CUDA;
+    if (grad_cost || grad_logits) {
+        const int gb = (int)std::min<int64_t>((n + 7) / 8, (int64_t)D->sms * 16);
+        rmb_grad_kernel<<<gb, 256, 0, s>>>((int)n, mdp->m, k, (float)mdp->gamma, pi, mdp->col, mdp->prob, V, lambda_out,
+                                           grad_cost, grad_logits);
+        g_launches++;
+        if (cudaGetLastError() != cudaSuccess) return RMB_ERR_CUDA;
+    }
+    if (stats && cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
+    return st;
 }
 
 const char* rmb_status_string(int status)
