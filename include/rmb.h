@@ -234,6 +234,55 @@ int rmb_fixed_point_grad(const rmb_mdp *mdp, const int32_t *pi, const float *V, 
                          const rmb_opts *opts, float *lambda_out, float *grad_cost, float *grad_logits,
                          void *workspace, size_t workspace_bytes, rmb_stats *stats, void *stream);
 
+/*
+ * Batched MB-VI: many independent MDPs (RMB_CSR) solved in one persistent launch (the paper has one
+ * MDP per solve; this runs its MB-VI, eq. (11), on each).  A host-side autotuner picks every MDP's
+ * batch size b (unless fixed) and the number of CTAs that solve it from a cost model, and packs small
+ * MDPs onto single CTAs longest-first.  Results per MDP are identical to rmb_vi with the same b, seed
+ * and options.
+ *
+ * 1. rmb_batched_workspace_bytes(items, count, opts): workspace size for this plan.
+ * 2. rmb_batched_plan(...): plans, writes the kernel parameters into the workspace (synchronous) and
+ *    fills *handle (plain data; keep it with the workspace).  plan_out (host, [count]) may be NULL.
+ * 3. rmb_batched_run(handle, stream): asynchronous solve of every MDP (capturable in a CUDA graph);
+ *    rmb_batched_graph_create / _launch / _destroy capture it once and replay it.
+ * 4. rmb_batched_results(handle, out[count], stream): waits, returns per-MDP stats and the first
+ *    non-OK status.
+ * Options: eps, max_sweeps, seed, start_sweep, barrier_timeout_ns and flags apply to every MDP.
+ */
+typedef struct {
+    rmb_mdp mdp;           /* RMB_CSR */
+    int64_t batch;         /* b for this MDP; 0 = autotuned */
+    float *V;              /* [n] device: start values in, solution out */
+    int32_t *pi;           /* [n] device greedy policy out, or NULL */
+    float *qgap;           /* [n] device Q-gap out, or NULL */
+} rmb_batch_item;
+
+typedef struct {
+    int64_t batch;         /* chosen b */
+    int32_t group_ctas;    /* CTAs solving this MDP together (1 = alone, packed with others) */
+    int32_t first_cta;
+    double est_ms;         /* cost-model estimate of this MDP's solve time */
+} rmb_batch_plan_item;
+
+typedef struct {
+    void *workspace;
+    int32_t count, grid_ctas, ntasks, reserved;
+    int64_t ctrl_offset, kp_offset, toff_offset, tasks_offset;
+    double est_ms;         /* cost-model makespan */
+} rmb_batch_handle;
+
+size_t rmb_batched_workspace_bytes(const rmb_batch_item *items, int count, const rmb_opts *opts);
+int rmb_batched_plan(const rmb_batch_item *items, int count, const rmb_opts *opts, void *workspace,
+                     size_t workspace_bytes, rmb_batch_handle *handle, rmb_batch_plan_item *plan_out,
+                     void *stream);
+int rmb_batched_run(const rmb_batch_handle *handle, void *stream);
+int rmb_batched_results(const rmb_batch_handle *handle, rmb_stats *out, void *stream);
+/* stream must be a created (non-default) stream; graph_exec receives a cudaGraphExec_t */
+int rmb_batched_graph_create(const rmb_batch_handle *handle, void *stream, void **graph_exec);
+int rmb_batched_graph_launch(void *graph_exec, void *stream);
+int rmb_batched_graph_destroy(void *graph_exec);
+
 /* Static text for a status code. */
 const char *rmb_status_string(int status);
 

@@ -69,6 +69,10 @@ def _rng(seed) -> np.random.Generator:
     return np.random.Generator(np.random.PCG64(seed))
 
 
+def _seq(seed) -> np.random.SeedSequence:
+    return seed if isinstance(seed, np.random.SeedSequence) else np.random.SeedSequence(seed)
+
+
 def _costs(rng, rows, dist):
     if dist == "uniform":
         return rng.random(rows).astype(np.float32)
@@ -84,7 +88,7 @@ def dense_dirichlet(n: int, m: int, alpha: float = 1.0, gamma: float = 0.95, see
     Rows are drawn blockwise from independent child seeds so memory stays bounded at large n.
     """
     rows = n * m
-    ss = np.random.SeedSequence(seed)
+    ss = _seq(seed)
     c_seq, p_seq = ss.spawn(2)
     cost = _costs(_rng(c_seq), rows, cost_dist)
     P = np.empty((rows, n), dtype=np.float32)
@@ -138,7 +142,7 @@ def csr_uniform_k(n: int, m: int, k: int, gamma: float = 0.99, seed: int = 0,
     """
     rows = n * m
     nnz = rows * k
-    ss = np.random.SeedSequence(seed)
+    ss = _seq(seed)
     c_seq, p_seq = ss.spawn(2)
     cost = _costs(_rng(c_seq), rows, cost_dist)
     col = np.empty(nnz, dtype=np.int32)

@@ -72,6 +72,23 @@ class rmb_stats(ctypes.Structure):
         return d
 
 
+class rmb_batch_item(ctypes.Structure):
+    _fields_ = [("mdp", rmb_mdp), ("batch", ctypes.c_int64), ("V", ctypes.c_void_p), ("pi", ctypes.c_void_p),
+                ("qgap", ctypes.c_void_p)]
+
+
+class rmb_batch_plan_item(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("group_ctas", ctypes.c_int32), ("first_cta", ctypes.c_int32),
+                ("est_ms", ctypes.c_double)]
+
+
+class rmb_batch_handle(ctypes.Structure):
+    _fields_ = [("workspace", ctypes.c_void_p), ("count", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("ntasks", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ctrl_offset", ctypes.c_int64),
+                ("kp_offset", ctypes.c_int64), ("toff_offset", ctypes.c_int64), ("tasks_offset", ctypes.c_int64),
+                ("est_ms", ctypes.c_double)]
+
+
 _LIB = None
 
 
@@ -395,3 +412,97 @@ def eval_policy(mdp: DeviceMDP, pi, opts: Opts, V0=None):
     V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda") if V0 is None else V0.clone()
     st = rmb_eval_policy(mdp, pi, opts, V)
     return {"V": V, "stats": st}
+
+
+# ----------------------------------------------------------------------------------------------
+# Batched MB-VI (many independent MDPs in one persistent launch).
+# ----------------------------------------------------------------------------------------------
+class Batch:
+    """A planned batched solve: holds the descriptors, the workspace and the handle."""
+
+    def __init__(self, mdps, Vs, opts: Opts, pis=None, gaps=None, batches=None, stream=None):
+        import torch
+        L = lib()
+        n = len(mdps)
+        self.mdps, self.Vs, self.pis, self.gaps = mdps, Vs, pis, gaps
+        arr = (rmb_batch_item * n)()
+        for i, dm in enumerate(mdps):
+            _check(Vs[i], torch.float32, dm.n, "V")
+            arr[i].mdp = dm.desc
+            arr[i].batch = 0 if batches is None else int(batches[i])
+            arr[i].V = _ptr(Vs[i])
+            arr[i].pi = _ptr(pis[i]) if pis is not None else None
+            arr[i].qgap = _ptr(gaps[i]) if gaps is not None else None
+        self.items = arr
+        self.opts = opts
+        o = opts.desc()
+        L.rmb_batched_workspace_bytes.argtypes = [ctypes.POINTER(rmb_batch_item), ctypes.c_int, ctypes.POINTER(rmb_opts)]
+        L.rmb_batched_workspace_bytes.restype = ctypes.c_size_t
+        nb = int(L.rmb_batched_workspace_bytes(arr, n, ctypes.byref(o)))
+        if nb == 0:
+            raise RmbError(RMB_ERR_ARG, "rmb_batched_workspace_bytes")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        self.handle = rmb_batch_handle()
+        self.plan = (rmb_batch_plan_item * n)()
+        f = L.rmb_batched_plan
+        f.argtypes = [ctypes.POINTER(rmb_batch_item), ctypes.c_int, ctypes.POINTER(rmb_opts), ctypes.c_void_p,
+                      ctypes.c_size_t, ctypes.POINTER(rmb_batch_handle), ctypes.POINTER(rmb_batch_plan_item),
+                      ctypes.c_void_p]
+        f.restype = ctypes.c_int
+        st = f(arr, n, ctypes.byref(o), _ptr(self.ws), nb, ctypes.byref(self.handle), self.plan,
+               _stream_handle(stream))
+        if st != RMB_OK:
+            raise RmbError(st, "rmb_batched_plan")
+        self.graph = None
+
+    def plan_table(self):
+        return [{"batch": p.batch, "group_ctas": p.group_ctas, "first_cta": p.first_cta, "est_ms": p.est_ms}
+                for p in self.plan]
+
+    def run(self, stream=None):
+        f = lib().rmb_batched_run
+        f.argtypes = [ctypes.POINTER(rmb_batch_handle), ctypes.c_void_p]
+        f.restype = ctypes.c_int
+        st = f(ctypes.byref(self.handle), _stream_handle(stream))
+        if st != RMB_OK:
+            raise RmbError(st, "rmb_batched_run")
+
+    def results(self, stream=None, check: bool = True):
+        n = self.handle.count
+        out = (rmb_stats * n)()
+        f = lib().rmb_batched_results
+        f.argtypes = [ctypes.POINTER(rmb_batch_handle), ctypes.POINTER(rmb_stats), ctypes.c_void_p]
+        f.restype = ctypes.c_int
+        st = f(ctypes.byref(self.handle), out, _stream_handle(stream))
+        if check and st not in (RMB_OK, RMB_ERR_NOT_CONVERGED):
+            raise RmbError(st, "rmb_batched_results")
+        return [out[i].as_dict() for i in range(n)]
+
+    def capture(self, stream):
+        """Capture the solve into a CUDA graph on `stream` (a torch.cuda.Stream, not the default)."""
+        L = lib()
+        ex = ctypes.c_void_p()
+        L.rmb_batched_graph_create.argtypes = [ctypes.POINTER(rmb_batch_handle), ctypes.c_void_p,
+                                               ctypes.POINTER(ctypes.c_void_p)]
+        L.rmb_batched_graph_create.restype = ctypes.c_int
+        st = L.rmb_batched_graph_create(ctypes.byref(self.handle), _stream_handle(stream), ctypes.byref(ex))
+        if st != RMB_OK:
+            raise RmbError(st, "rmb_batched_graph_create")
+        self.graph = ex
+
+    def replay(self, stream):
+        L = lib()
+        L.rmb_batched_graph_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+        L.rmb_batched_graph_launch.restype = ctypes.c_int
+        st = L.rmb_batched_graph_launch(self.graph, _stream_handle(stream))
+        if st != RMB_OK:
+            raise RmbError(st, "rmb_batched_graph_launch")
+
+    def __del__(self):
+        try:
+            if self.graph is not None:
+                L = lib()
+                L.rmb_batched_graph_destroy.argtypes = [ctypes.c_void_p]
+                L.rmb_batched_graph_destroy(self.graph)
+        except Exception:
+            pass

@@ -27,7 +27,9 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "rmb.h"
 #include "rmb_device.cuh"
@@ -246,14 +248,14 @@ __device__ __forceinline__ void state_epilogue(const KP& p, const Best& r, int s
 // Unit = a group of lps lanes; position i of the batch goes to unit (i mod U), step (i div U).
 // ------------------------------------------------------------------------------------------------
 template <int KIND, bool VEC>
-__device__ void csr_batch(const KP& p, int lps, const float* __restrict__ A, float* B, int pos0, int len,
-                          const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc,
+__device__ void csr_batch(const KP& p, const GroupView& gv, int lps, const float* __restrict__ A, float* B, int pos0,
+                          int len, const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc,
                           bool* perm_ok)
 {
     constexpr bool ARG = (KIND == K_GREEDY);
     const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int warp = (gv.rank * (int)blockDim.x + (int)threadIdx.x) >> 5;
+    const int nwarps = (gv.size * (int)blockDim.x) >> 5;
     const int spw = 32 / lps;
     const int g = lane / lps, lane_g = lane - g * lps;
     const int U = nwarps * spw;
@@ -364,11 +366,11 @@ __device__ __forceinline__ Best fast_eval(const KP& p, const StateRegs<NC>& R, c
 
 struct FastGeom {
     int lane, spw, per_block, g, lane_g, U, first, my_off, my_step;
-    __device__ FastGeom(int lps)
+    __device__ FastGeom(int lps, const GroupView& gv)
     {
         lane = threadIdx.x & 31;
-        const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-        const int nwarps = (gridDim.x * blockDim.x) >> 5;
+        const int warp = (gv.rank * (int)blockDim.x + (int)threadIdx.x) >> 5;
+        const int nwarps = (gv.size * (int)blockDim.x) >> 5;
         spw = 32 / lps;
         per_block = 32 / spw;          // steps covered by one permutation evaluation per lane
         g = lane / lps;
@@ -388,10 +390,10 @@ struct FastGeom {
 
 // resolve and load this warp's first state of a batch ahead of time
 template <int KIND, int NC>
-__device__ __forceinline__ void fast_prefetch_first(const KP& p, int lps, int pos0, int len, const PermKey* K,
-                                                    Carry<NC>& carry, bool* perm_ok)
+__device__ __forceinline__ void fast_prefetch_first(const KP& p, const GroupView& gv, int lps, int pos0, int len,
+                                                    const PermKey* K, Carry<NC>& carry, bool* perm_ok)
 {
-    const FastGeom G(lps);
+    const FastGeom G(lps, gv);
     carry.valid = false;
     if (G.first >= len) return;
     carry.block_states = G.resolve(0, pos0, len, K, perm_ok);
@@ -401,13 +403,13 @@ __device__ __forceinline__ void fast_prefetch_first(const KP& p, int lps, int po
 }
 
 template <int KIND, int NC>
-__device__ void csr_batch_fast(const KP& p, int lps, const float* __restrict__ A, float* B, int pos0, int len,
-                               const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc, bool* perm_ok,
-                               Carry<NC>& carry)
+__device__ void csr_batch_fast(const KP& p, const GroupView& gv, int lps, const float* __restrict__ A, float* B,
+                               int pos0, int len, const PermKey* K, int32_t* Sout, float* Wout, const Centre& C,
+                               Acc& acc, bool* perm_ok, Carry<NC>& carry)
 {
     constexpr bool ARG = (KIND == K_GREEDY);
     constexpr int LK = (KIND == K_POLICY) ? K_POLICY : K_MIN;   // which rows to load
-    const FastGeom G(lps);
+    const FastGeom G(lps, gv);
     if (G.first >= len) { carry.valid = false; return; }
     int block_states, s_cur;
     StateRegs<NC> cur, nxt;
@@ -584,19 +586,20 @@ __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole
 }
 
 template <int KIND, bool VEC>
-__device__ bool dense_batch(const KP& p, DenseSmem& sm, float* stage, const float* A, float* B, int pos0,
-                            int len, const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc,
-                            bool* perm_ok)
+__device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, float* stage, const float* A, float* B,
+                            int pos0, int len, const PermKey* K, int32_t* Sout, float* Wout, const Centre& C,
+                            Acc& acc, bool* perm_ok)
 {
     const bool whole = p.n <= p.stage;
-    const int G = gridDim.x;
-    if ((int)blockIdx.x >= len) return true;
+    const int G = gv.size;
+    const int me = gv.rank;
+    if (me >= len) return true;
     bool ok = true;
     if (whole && !stage_values(p, sm, stage, A, (p.n + 3) & ~3)) return false;
-    for (int j0 = 0; (int)blockIdx.x + j0 * G < len; j0 += 32) {
+    for (int j0 = 0; me + j0 * G < len; j0 += 32) {
         __syncthreads();
         if (threadIdx.x < 32) {
-            const int pos = (int)blockIdx.x + (j0 + (int)threadIdx.x) * G;
+            const int pos = me + (j0 + (int)threadIdx.x) * G;
             int st = -1;
             if (pos < len) st = K ? state_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
             sm.perm[threadIdx.x] = st;
@@ -611,7 +614,7 @@ __device__ bool dense_batch(const KP& p, DenseSmem& sm, float* stage, const floa
             const Best r = dense_state<KIND, VEC>(p, sm, stage, whole, A, s, pi_s, &ok);
             if (!ok) return false;
             if (threadIdx.x == 0)
-                state_epilogue<KIND>(p, r, s, (int)blockIdx.x + (j0 + jj) * G, A, B, Sout, Wout, C, acc);
+                state_epilogue<KIND>(p, r, s, me + (j0 + jj) * G, A, B, Sout, Wout, C, acc);
         }
     }
     return true;
@@ -681,10 +684,12 @@ struct Runner {
     DenseSmem* dsm;
     float* stage;
     bool perm_ok;
+    GroupView gv;
+    bool lead;   // thread 0 of the group's first CTA
 
-    __device__ Runner(const KP& kp, RedSmem& r, DenseSmem* d, float* st)
+    __device__ Runner(const KP& kp, RedSmem& r, DenseSmem* d, float* st, GroupView g)
         : p(kp), c(kp.ctrl), target(0), barriers(0), stall(false), cur(0), red_epoch(0), rs(r), dsm(d),
-          stage(st), perm_ok(true)
+          stage(st), perm_ok(true), gv(g), lead(g.rank == 0 && threadIdx.x == 0)
     {
         carry_a.valid = false;
         carry_o.valid = false;
@@ -703,12 +708,12 @@ struct Runner {
         stall = false;
         if (!perm_ok) atomicCAS(&c->error, 0, RMB_ERR_UNSUPPORTED);
         ++barriers;
-        grid_arrive(c, target, skip);
+        grid_arrive(c, target, skip, gv.size);
     }
-    __device__ bool wait(int site) { return grid_wait_arrived(c, target, p.timeout_ns, site); }
+    __device__ bool wait(int site) { return grid_wait_arrived(c, target, p.timeout_ns, site, gv.size); }
 
-    __device__ size_t gtid() const { return (size_t)blockIdx.x * blockDim.x + threadIdx.x; }
-    __device__ size_t gthreads() const { return (size_t)gridDim.x * blockDim.x; }
+    __device__ size_t gtid() const { return (size_t)gv.rank * blockDim.x + threadIdx.x; }
+    __device__ size_t gthreads() const { return (size_t)gv.size * blockDim.x; }
 
     static constexpr int NCA_ = NCA > 0 ? NCA : 1;
     static constexpr int NCO_ = NCO > 0 ? NCO : 1;
@@ -721,21 +726,21 @@ struct Runner {
     {
         if (PATH == PATH_DENSE) {
             if (p.n % 4 == 0 && (((uintptr_t)p.P) & 15) == 0)
-                return dense_batch<KIND, true>(p, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
-            return dense_batch<KIND, false>(p, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+                return dense_batch<KIND, true>(p, gv, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+            return dense_batch<KIND, false>(p, gv, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
         } else {
             const int lps = (KIND == K_POLICY) ? p.lps_one : p.lps_all;
             if (PATH == PATH_CSR_VEC && KIND == K_POLICY && NCO > 0) {
-                csr_batch_fast<K_POLICY, NCO_>(p, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok, carry_o);
+                csr_batch_fast<K_POLICY, NCO_>(p, gv, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok, carry_o);
                 return true;
             }
             if (PATH == PATH_CSR_VEC && KIND != K_POLICY && NCA > 0) {
                 carry_a.valid = carry_a.valid && KIND == K_MIN;
-                csr_batch_fast<KIND == K_GREEDY ? K_GREEDY : K_MIN, NCA_>(p, lps, A, B, pos0, len, K, So, Wo, C, acc,
-                                                                         &perm_ok, carry_a);
+                csr_batch_fast<KIND == K_GREEDY ? K_GREEDY : K_MIN, NCA_>(p, gv, lps, A, B, pos0, len, K, So, Wo, C,
+                                                                         acc, &perm_ok, carry_a);
                 return true;
             }
-            csr_batch<KIND, PATH == PATH_CSR_VEC>(p, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+            csr_batch<KIND, PATH == PATH_CSR_VEC>(p, gv, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
             return true;
         }
     }
@@ -745,8 +750,9 @@ struct Runner {
     __device__ void prefetch_next(int pos0, int len, const PermKey* K)
     {
         if (PATH != PATH_CSR_VEC) return;
-        if (KIND == K_POLICY && NCO > 0) fast_prefetch_first<K_POLICY, NCO_>(p, p.lps_one, pos0, len, K, carry_o, &perm_ok);
-        if (KIND == K_MIN && NCA > 0) fast_prefetch_first<K_MIN, NCA_>(p, p.lps_all, pos0, len, K, carry_a, &perm_ok);
+        if (KIND == K_POLICY && NCO > 0)
+            fast_prefetch_first<K_POLICY, NCO_>(p, gv, p.lps_one, pos0, len, K, carry_o, &perm_ok);
+        if (KIND == K_MIN && NCA > 0) fast_prefetch_first<K_MIN, NCA_>(p, gv, p.lps_all, pos0, len, K, carry_a, &perm_ok);
     }
 
     __device__ void copy_batch(const int32_t* S, const float* Wv, int len, float* B)
@@ -799,7 +805,7 @@ struct Runner {
         PermKey K = key_for(k);
         K.buf = p.perm_buf;
         const int slot = red_epoch % 3;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (lead) {
             const int nxt = (red_epoch + 1) % 3;
             c->red_delta[nxt] = 0u;
             c->red_hi[nxt] = 0u;
@@ -822,7 +828,7 @@ struct Runner {
         float lo, hi;
         read_slot(c, slot, rs, delta, lo, hi);
         const int newcur = (cur + p.T) & 1;
-        if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace && j >= 0) p.trace[j] = (double)delta;
+        if (lead && p.trace && j >= 0) p.trace[j] = (double)delta;
         stop = can_stop && ((double)delta <= p.eps || is_last);
         if (delta != delta) {
             atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
@@ -856,7 +862,7 @@ struct Runner {
     __device__ bool greedy_pass(float& resid, long long next_k = -1)
     {
         const int slot = red_epoch % 3;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (lead) {
             const int nxt = (red_epoch + 1) % 3;
             c->red_delta[nxt] = 0u;
             c->red_hi[nxt] = 0u;
@@ -887,7 +893,7 @@ struct Runner {
 
     __device__ void run()
     {
-        stall = (p.flags & RMB_FLAG_INJECT_BARRIER_STALL) && blockIdx.x == 0;
+        stall = (p.flags & RMB_FLAG_INJECT_BARRIER_STALL) && gv.rank == 0;
         if (PATH == PATH_DENSE && threadIdx.x == 0) {
             const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&dsm->mbar);
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
@@ -958,7 +964,7 @@ struct Runner {
             float r;
             if (!greedy_pass(r, p.start_sweep + sweeps)) return finish(false, sweeps, iters, residual);   // also writes V
             residual = (double)r;
-            if (blockIdx.x == 0 && threadIdx.x == 0 && p.trace) p.trace[iters] = residual;
+            if (lead && p.trace) p.trace[iters] = residual;
             ++iters;
             if (residual <= p.eps) { converged = true; break; }
             if (iters >= p.max_sweeps) break;
@@ -975,7 +981,7 @@ struct Runner {
 
     __device__ void finish(bool ok, long long sweeps, long long iters, double residual, bool converged = false)
     {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (lead) {
             c->sweeps = sweeps;
             c->iters = iters;
             c->barriers = barriers;
@@ -994,14 +1000,14 @@ template <int NCA, int NCO>
 __global__ void __launch_bounds__(kCsrThreads, 1) rmb_csr_vec_kernel(KP p)
 {
     __shared__ RedSmem rs;
-    Runner<PATH_CSR_VEC, NCA, NCO> R(p, rs, nullptr, nullptr);
+    Runner<PATH_CSR_VEC, NCA, NCO> R(p, rs, nullptr, nullptr, GroupView{(int)blockIdx.x, (int)gridDim.x});
     R.run();
 }
 
 __global__ void __launch_bounds__(kCsrThreads, 2) rmb_csr_gen_kernel(KP p)
 {
     __shared__ RedSmem rs;
-    Runner<PATH_CSR_GEN> R(p, rs, nullptr, nullptr);
+    Runner<PATH_CSR_GEN> R(p, rs, nullptr, nullptr, GroupView{(int)blockIdx.x, (int)gridDim.x});
     R.run();
 }
 
@@ -1010,8 +1016,42 @@ __global__ void __launch_bounds__(kDenseThreads, 3) rmb_dense_kernel(KP p)
     __shared__ RedSmem rs;
     __shared__ __align__(16) DenseSmem dsm;
     extern __shared__ __align__(128) float stage[];
-    Runner<PATH_DENSE> R(p, rs, &dsm, stage);
+    Runner<PATH_DENSE> R(p, rs, &dsm, stage, GroupView{(int)blockIdx.x, (int)gridDim.x});
     R.run();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Batched solves: many independent MDPs in one persistent launch.  Every CTA runs a list of tasks; a
+// task is one MDP solved by a group of CTAs (its own barrier counter and control block) or by this
+// CTA alone (barriers are then CTA barriers).  CTAs of a multi-CTA group run the same task list.
+// ------------------------------------------------------------------------------------------------
+struct BatchTask {
+    int item, rank, size, pad;
+};
+
+__global__ void __launch_bounds__(kCsrThreads, 1)
+rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off, const BatchTask* __restrict__ tasks)
+{
+    __shared__ RedSmem rs;
+    __shared__ KP s_kp;
+    const int t0 = task_off[blockIdx.x], t1 = task_off[blockIdx.x + 1];
+    for (int t = t0; t < t1; ++t) {
+        const BatchTask bt = tasks[t];
+        __syncthreads();
+        if (threadIdx.x == 0) s_kp = kps[bt.item];
+        __syncthreads();
+        const GroupView gv{bt.rank, bt.size};
+        if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 1 && s_kp.nc_one == 1) {
+            Runner<PATH_CSR_VEC, 1, 1> R(s_kp, rs, nullptr, nullptr, gv);
+            R.run();
+        } else if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 2 && s_kp.nc_one == 1) {
+            Runner<PATH_CSR_VEC, 2, 1> R(s_kp, rs, nullptr, nullptr, gv);
+            R.run();
+        } else {
+            Runner<PATH_CSR_GEN> R(s_kp, rs, nullptr, nullptr, gv);
+            R.run();
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1379,33 +1419,10 @@ int launch_validate(const rmb_mdp* M, int* err, cudaStream_t st, int sms)
     return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
 }
 
-int solve(const Call& q)
+// Kernel parameters of one solve: problem, schedule, workspace buffers at `ws` (laid out as L), the
+// control block `ctrl`.  The caller sets the value / policy pointers.  Returns the row path.
+int fill_kp(int mode, const rmb_mdp* M, const rmb_opts* O, int64_t b, char* ws, const Layout& L, Ctrl* ctrl, KP& p)
 {
-    int st = check_mdp(q.M);
-    if (st) return st;
-    const rmb_mdp* M = q.M;
-    const rmb_opts* O = q.O;
-    if (!O) return RMB_ERR_ARG;
-    int64_t b = M->n;
-    if (q.mode != MODE_GREEDY) {
-        if ((st = effective_batch(M, O, &b))) return st;
-        if (O->max_sweeps < 1) return RMB_ERR_ARG;
-        if (!(O->eps >= 0.0) || std::isinf(O->eps)) return RMB_ERR_ARG;
-        if (q.mode == MODE_MPI && (O->eval_sweeps < 1 || !q.pi)) return RMB_ERR_ARG;
-        if (q.mode == MODE_EVAL && !q.pi_in) return RMB_ERR_ARG;
-        if (O->start_sweep < 0) return RMB_ERR_ARG;
-    }
-    if (!q.Vin) return RMB_ERR_ARG;
-    if (O->grid_ctas < 0 || O->barrier_timeout_ns < 0) return RMB_ERR_ARG;
-    const Layout L = layout(M->n, b);
-    if (!q.ws || ((uintptr_t)q.ws & 255)) return RMB_ERR_WORKSPACE;
-    if (q.ws_bytes < L.total) return RMB_ERR_WORKSPACE;
-
-    DevInfo* D = nullptr;
-    if ((st = dev_info(&D))) return st;
-
-    char* ws = static_cast<char*>(q.ws);
-    KP p;
     std::memset(&p, 0, sizeof(p));
     p.n = (int)M->n;
     p.m = M->m;
@@ -1417,32 +1434,26 @@ int solve(const Call& q)
     p.cost = M->cost;
     p.gamma = (float)M->gamma;
     p.gamma_d = M->gamma;
-    p.mode = q.mode;
+    p.mode = mode;
     p.b = (int)b;
     p.T = (int)((M->n + b - 1) / b);
     p.last_len = (int)(M->n - (int64_t)(p.T - 1) * b);
     p.K = O->eval_sweeps;
     p.start_sweep = O->start_sweep;
-    p.max_sweeps = q.mode == MODE_GREEDY ? 0 : O->max_sweeps;
+    p.max_sweeps = mode == MODE_GREEDY ? 0 : O->max_sweeps;
     p.eps = O->eps;
     p.seed_lo = (uint32_t)O->seed;
     p.seed_hi = (uint32_t)(O->seed >> 32);
     p.h = perm_half_bits(M->n);
-    p.Vin = q.Vin;
-    p.Vout = q.Vout;
-    p.TVout = q.TV;
-    p.pi = q.pi;
-    p.qgap = q.qgap;
-    p.pi_in = q.pi_in;
     p.d[0] = reinterpret_cast<float*>(ws + L.d0);
     p.d[1] = reinterpret_cast<float*>(ws + L.d1);
     p.S[0] = reinterpret_cast<int32_t*>(ws + L.s0);
     p.S[1] = reinterpret_cast<int32_t*>(ws + L.s1);
     p.W[0] = reinterpret_cast<float*>(ws + L.w0);
     p.W[1] = reinterpret_cast<float*>(ws + L.w1);
-    p.perm_buf = (L.perm_buf && q.mode != MODE_GREEDY) ? reinterpret_cast<int32_t*>(ws + L.pb) : nullptr;
-    p.ctrl = reinterpret_cast<Ctrl*>(ws + L.ctrl);
-    p.trace = q.mode == MODE_GREEDY ? nullptr : O->trace;
+    p.perm_buf = (L.perm_buf && mode != MODE_GREEDY) ? reinterpret_cast<int32_t*>(ws + L.pb) : nullptr;
+    p.ctrl = ctrl;
+    p.trace = mode == MODE_GREEDY ? nullptr : O->trace;
     p.timeout_ns = O->barrier_timeout_ns > 0 ? O->barrier_timeout_ns : 2000000000LL;
     p.flags = O->flags;
 
@@ -1472,6 +1483,44 @@ int solve(const Call& q)
         p.lps_one = 32;
         p.lps_all = 32;
     }
+
+    return path;
+}
+
+int solve(const Call& q)
+{
+    int st = check_mdp(q.M);
+    if (st) return st;
+    const rmb_mdp* M = q.M;
+    const rmb_opts* O = q.O;
+    if (!O) return RMB_ERR_ARG;
+    int64_t b = M->n;
+    if (q.mode != MODE_GREEDY) {
+        if ((st = effective_batch(M, O, &b))) return st;
+        if (O->max_sweeps < 1) return RMB_ERR_ARG;
+        if (!(O->eps >= 0.0) || std::isinf(O->eps)) return RMB_ERR_ARG;
+        if (q.mode == MODE_MPI && (O->eval_sweeps < 1 || !q.pi)) return RMB_ERR_ARG;
+        if (q.mode == MODE_EVAL && !q.pi_in) return RMB_ERR_ARG;
+        if (O->start_sweep < 0) return RMB_ERR_ARG;
+    }
+    if (!q.Vin) return RMB_ERR_ARG;
+    if (O->grid_ctas < 0 || O->barrier_timeout_ns < 0) return RMB_ERR_ARG;
+    const Layout L = layout(M->n, b);
+    if (!q.ws || ((uintptr_t)q.ws & 255)) return RMB_ERR_WORKSPACE;
+    if (q.ws_bytes < L.total) return RMB_ERR_WORKSPACE;
+
+    DevInfo* D = nullptr;
+    if ((st = dev_info(&D))) return st;
+
+    char* ws = static_cast<char*>(q.ws);
+    KP p;
+    const int path = fill_kp(q.mode, M, O, b, ws, L, reinterpret_cast<Ctrl*>(ws + L.ctrl), p);
+    p.Vin = q.Vin;
+    p.Vout = q.Vout;
+    p.TVout = q.TV;
+    p.pi = q.pi;
+    p.qgap = q.qgap;
+    p.pi_in = q.pi_in;
 
     const void* fn;
     int threads, per_sm;
@@ -1566,9 +1615,393 @@ int noalloc_scratch(void** out)
     return RMB_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Batched solves: autotuner and plan.
+//
+// Cost model of one MDP solved by G CTAs with batch b (times in microseconds):
+//   sweeps(b)  = 0.85 ln(eps) / ln(gamma) * (0.65 + 0.35 (b/n)^0.835)   (VI from V = 0, costs in [0,1];
+//                the b-dependence is the fit to the measured sweeps-to-1e-6 of the n = 2^20 CSR MDP)
+//   batch time = latency(G) + max(steps * 2.0, b * bytes_per_state / (13000 * G))
+//                latency(1) = 1.2 (CTA barrier), latency(G > 1) = 5.0 (grid-group barrier);
+//                steps = ceil(b / (states a group processes at once)); 13 GB/s = one SM's share of the
+//                measured P-stream rate
+//   time       = sweeps(b) * ceil(n/b) * batch time
+// Each MDP gets the b minimising its time (unless the caller fixed b).  The makespan target M is
+// found by bisection: MDPs whose single-CTA time exceeds M get the smallest group that meets M, the
+// others are packed onto the remaining CTAs longest-first (LPT); M is feasible if every CTA meets it.
+// ------------------------------------------------------------------------------------------------
+struct ItemCost {
+    int64_t n;
+    double bytes_per_state, gamma;
+    int concurrency_per_cta;   // states one CTA processes at once
+};
+
+double est_sweeps(double gamma, double eps, double frac)
+{
+    const double e = eps > 1e-12 ? eps : 1e-12;
+    const double base = 0.85 * std::log(e) / std::log(gamma);
+    const double s = base * (0.65 + 0.35 * std::pow(frac, 0.835));
+    return s > 1.0 ? s : 1.0;
+}
+
+double est_time_us(const ItemCost& c, int64_t b, int G, double eps)
+{
+    const double T = (double)((c.n + b - 1) / b);
+    const double conc = (double)c.concurrency_per_cta * G;
+    const double steps = std::ceil((double)b / conc);
+    const double lat = G == 1 ? 1.2 : 5.0;
+    const double stream = (double)b * c.bytes_per_state / (13000.0 * G);
+    const double per_batch = lat + (steps * 2.0 > stream ? steps * 2.0 : stream);
+    return est_sweeps(c.gamma, eps, (double)b / (double)c.n) * T * per_batch;
+}
+
+struct ItemPlan {
+    int64_t b;
+    int G;
+    double t;
+};
+
+ItemPlan best_b(const ItemCost& c, int G, double eps, int64_t fixed_b)
+{
+    ItemPlan best{c.n, G, 1e300};
+    if (fixed_b > 0) {
+        best.b = fixed_b > c.n ? c.n : fixed_b;
+        best.t = est_time_us(c, best.b, G, eps);
+        return best;
+    }
+    for (int64_t b = c.n;; b = (b + 1) / 2) {
+        const double t = est_time_us(c, b, G, eps);
+        if (t < best.t) best = ItemPlan{b, G, t};
+        if (b <= 32) break;
+    }
+    return best;
+}
+
+struct BatchPlan {
+    std::vector<ItemPlan> items;
+    std::vector<int> first_cta;
+    std::vector<int> task_off;
+    std::vector<BatchTask> tasks;
+    double makespan;
+};
+
+bool try_makespan(const std::vector<ItemCost>& cs, const std::vector<int64_t>& fixed, int ctas, double eps, double M,
+                  BatchPlan* out)
+{
+    const int N = (int)cs.size();
+    std::vector<ItemPlan> ip(N);
+    std::vector<int> big, small;
+    int used = 0;
+    for (int i = 0; i < N; ++i) {
+        const ItemPlan one = best_b(cs[i], 1, eps, fixed[i]);
+        if (one.t <= M) {
+            ip[i] = one;
+            small.push_back(i);
+            continue;
+        }
+        bool ok = false;
+        for (int G = 2; G <= ctas; G = G < 8 ? G + 1 : G + G / 4) {
+            const ItemPlan pg = best_b(cs[i], G, eps, fixed[i]);
+            if (pg.t <= M) {
+                ip[i] = pg;
+                ok = true;
+                break;
+            }
+        }
+        if (!ok) return false;
+        used += ip[i].G;
+        big.push_back(i);
+    }
+    const int free_ctas = ctas - used;
+    if (free_ctas < 0 || (free_ctas == 0 && !small.empty())) return false;
+    std::sort(small.begin(), small.end(), [&](int a, int b) { return ip[a].t > ip[b].t; });
+    std::vector<double> load(free_ctas > 0 ? free_ctas : 0, 0.0);
+    std::vector<std::vector<int>> bins(load.size());
+    for (int i : small) {
+        int best = 0;
+        for (int c = 1; c < (int)load.size(); ++c)
+            if (load[c] < load[best]) best = c;
+        load[best] += ip[i].t;
+        bins[best].push_back(i);
+        if (load[best] > M) return false;
+    }
+    if (!out) return true;
+    out->items = ip;
+    out->first_cta.assign(N, -1);
+    out->task_off.assign(ctas + 1, 0);
+    out->tasks.clear();
+    std::vector<std::vector<BatchTask>> per(ctas);
+    int cta = 0;
+    double mk = 0.0;
+    for (int i : big) {
+        out->first_cta[i] = cta;
+        for (int r = 0; r < ip[i].G; ++r) per[cta + r].push_back(BatchTask{i, r, ip[i].G, 0});
+        cta += ip[i].G;
+        mk = ip[i].t > mk ? ip[i].t : mk;
+    }
+    for (size_t bI = 0; bI < bins.size(); ++bI) {
+        for (int i : bins[bI]) {
+            out->first_cta[i] = cta + (int)bI;
+            per[cta + bI].push_back(BatchTask{i, 0, 1, 0});
+        }
+        mk = load[bI] > mk ? load[bI] : mk;
+    }
+    for (int c = 0; c < ctas; ++c) {
+        out->task_off[c + 1] = out->task_off[c] + (int)per[c].size();
+        for (const BatchTask& t : per[c]) out->tasks.push_back(t);
+    }
+    out->makespan = mk;
+    return true;
+}
+
+int make_batch_plan(const rmb_batch_item* items, int count, const rmb_opts* O, int ctas, BatchPlan* plan)
+{
+    std::vector<ItemCost> cs(count);
+    std::vector<int64_t> fixed(count);
+    double lo = 0.0, hi = 0.0;
+    for (int i = 0; i < count; ++i) {
+        const rmb_mdp* M = &items[i].mdp;
+        const int64_t nnz_row = M->format == RMB_CSR ? (M->k_uniform > 0 ? M->k_uniform : 16) : M->n;
+        cs[i].n = M->n;
+        cs[i].gamma = M->gamma;
+        cs[i].bytes_per_state = (double)M->m * (double)nnz_row * 8.0 + 4.0 * M->m;
+        int lps = 32;
+        if (csr_vec_ok(M)) {
+            const int k4 = M->k_uniform >> 2;
+            const int cpr = k4 < 32 ? k4 : 32;
+            const int all = pow2ceil(cpr * M->m);
+            lps = all > 32 ? 32 : all;
+        }
+        cs[i].concurrency_per_cta = (kCsrThreads / 32) * (32 / lps);
+        fixed[i] = items[i].batch;
+        const ItemPlan one = best_b(cs[i], 1, O->eps, fixed[i]);
+        lo += one.t;
+        hi = one.t > hi ? one.t : hi;
+    }
+    lo /= ctas;
+    if (hi < lo) hi = lo;
+    hi *= 2.0;
+    if (!try_makespan(cs, fixed, ctas, O->eps, hi, nullptr)) {
+        // even the slowest single-CTA time is infeasible with these CTAs: grow until feasible
+        int guard = 0;
+        while (!try_makespan(cs, fixed, ctas, O->eps, hi, nullptr) && guard++ < 60) hi *= 2.0;
+        if (guard >= 60) return RMB_ERR_UNSUPPORTED;
+    }
+    for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (try_makespan(cs, fixed, ctas, O->eps, mid, nullptr)) hi = mid;
+        else lo = mid;
+        if (hi - lo < 1e-3 * hi) break;
+    }
+    return try_makespan(cs, fixed, ctas, O->eps, hi, plan) ? RMB_OK : RMB_ERR_UNSUPPORTED;
+}
+
+struct BatchLayout {
+    size_t ctrl, kps, toff, tasks, items0, total;
+    std::vector<size_t> item_off;
+};
+
+BatchLayout batch_layout(const rmb_batch_item* items, int count, const BatchPlan& plan, int ctas)
+{
+    BatchLayout B;
+    B.ctrl = 256;
+    B.kps = B.ctrl + align_up((size_t)count * sizeof(Ctrl), 256);
+    B.toff = B.kps + align_up((size_t)count * sizeof(KP), 256);
+    B.tasks = B.toff + align_up((size_t)(ctas + 1) * sizeof(int), 256);
+    B.items0 = B.tasks + align_up((size_t)plan.tasks.size() * sizeof(BatchTask) + 16, 256);
+    size_t off = B.items0;
+    B.item_off.resize(count);
+    for (int i = 0; i < count; ++i) {
+        B.item_off[i] = off;
+        off += layout(items[i].mdp.n, plan.items[i].b).total;
+    }
+    B.total = off;
+    return B;
+}
+
+int check_batch(const rmb_batch_item* items, int count, const rmb_opts* O)
+{
+    if (!items || count < 1 || !O) return RMB_ERR_ARG;
+    if (O->max_sweeps < 1 || !(O->eps >= 0.0) || std::isinf(O->eps) || O->start_sweep < 0) return RMB_ERR_ARG;
+    for (int i = 0; i < count; ++i) {
+        const int st = check_mdp(&items[i].mdp);
+        if (st) return st;
+        if (items[i].mdp.format != RMB_CSR) return RMB_ERR_UNSUPPORTED;
+        if (!items[i].V || items[i].batch < 0) return RMB_ERR_ARG;
+    }
+    return RMB_OK;
+}
+
+int batched_ctas(int* ctas)
+{
+    DevInfo* D = nullptr;
+    int st = dev_info(&D);
+    if (st) return st;
+    cudaFuncSetAttribute(rmb_batched_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rmb_batched_kernel, kCsrThreads, 0) != cudaSuccess || occ < 1)
+        return RMB_ERR_CUDA;
+    *ctas = D->sms;   // one CTA per SM (the kernel is register-bound to one 512-thread CTA per SM)
+    return RMB_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+size_t rmb_batched_workspace_bytes(const rmb_batch_item* items, int count, const rmb_opts* opts)
+{
+    if (check_batch(items, count, opts)) return 0;
+    int ctas = 0;
+    if (batched_ctas(&ctas)) return 0;
+    BatchPlan plan;
+    if (make_batch_plan(items, count, opts, ctas, &plan)) return 0;
+    return batch_layout(items, count, plan, ctas).total;
+}
+
+int rmb_batched_plan(const rmb_batch_item* items, int count, const rmb_opts* opts, void* workspace,
+                     size_t workspace_bytes, rmb_batch_handle* handle, rmb_batch_plan_item* plan_out, void* stream)
+{
+    int st = check_batch(items, count, opts);
+    if (st) return st;
+    if (!handle) return RMB_ERR_ARG;
+    int ctas = 0;
+    if ((st = batched_ctas(&ctas))) return st;
+    BatchPlan plan;
+    if ((st = make_batch_plan(items, count, opts, ctas, &plan))) return st;
+    const BatchLayout B = batch_layout(items, count, plan, ctas);
+    if (!workspace || ((uintptr_t)workspace & 255)) return RMB_ERR_WORKSPACE;
+    if (workspace_bytes < B.total) return RMB_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    std::vector<KP> kps(count);
+    for (int i = 0; i < count; ++i) {
+        const rmb_mdp* M = &items[i].mdp;
+        const Layout L = layout(M->n, plan.items[i].b);
+        rmb_opts oi = *opts;
+        oi.batch = plan.items[i].b;
+        oi.trace = nullptr;
+        fill_kp(MODE_VI, M, &oi, plan.items[i].b, ws + B.item_off[i], L,
+                reinterpret_cast<Ctrl*>(ws + B.ctrl) + i, kps[i]);
+        if (kps[i].path == PATH_CSR_VEC && !((kps[i].nc_all == 1 || kps[i].nc_all == 2) && kps[i].nc_one == 1)) {
+            if (!M->row_ptr) return RMB_ERR_UNSUPPORTED;
+            kps[i].path = PATH_CSR_GEN;
+            kps[i].lps_all = kps[i].lps_one = 32;
+        }
+        kps[i].Vin = items[i].V;
+        kps[i].Vout = items[i].V;
+        kps[i].pi = items[i].pi;
+        kps[i].qgap = items[i].qgap;
+        if (plan_out) {
+            plan_out[i].batch = plan.items[i].b;
+            plan_out[i].group_ctas = plan.items[i].G;
+            plan_out[i].first_cta = plan.first_cta[i];
+            plan_out[i].est_ms = plan.items[i].t / 1e3;
+        }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(ws + B.kps, kps.data(), kps.size() * sizeof(KP), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + B.toff, plan.task_off.data(), plan.task_off.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess ||
+        cudaMemcpyAsync(ws + B.tasks, plan.tasks.data(), plan.tasks.size() * sizeof(BatchTask), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess)
+        return RMB_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
+    std::memset(handle, 0, sizeof(*handle));
+    handle->workspace = workspace;
+    handle->count = count;
+    handle->grid_ctas = ctas;
+    handle->ntasks = (int32_t)plan.tasks.size();
+    handle->ctrl_offset = (int64_t)B.ctrl;
+    handle->kp_offset = (int64_t)B.kps;
+    handle->toff_offset = (int64_t)B.toff;
+    handle->tasks_offset = (int64_t)B.tasks;
+    handle->est_ms = plan.makespan / 1e3;
+    return RMB_OK;
+}
+
+int rmb_batched_run(const rmb_batch_handle* h, void* stream)
+{
+    if (!h || !h->workspace || h->count < 1 || h->grid_ctas < 1) return RMB_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    char* ws = static_cast<char*>(h->workspace);
+    if (cudaMemsetAsync(ws + h->ctrl_offset, 0, (size_t)h->count * sizeof(Ctrl), s) != cudaSuccess) return RMB_ERR_CUDA;
+    const KP* kps = reinterpret_cast<const KP*>(ws + h->kp_offset);
+    const int* toff = reinterpret_cast<const int*>(ws + h->toff_offset);
+    const BatchTask* tasks = reinterpret_cast<const BatchTask*>(ws + h->tasks_offset);
+    void* args[] = {(void*)&kps, (void*)&toff, (void*)&tasks};
+    const cudaError_t ce = cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(rmb_batched_kernel),
+                                                       dim3(h->grid_ctas), dim3(kCsrThreads), args, 0, s);
+    g_launches++;
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return RMB_ERR_CUDA;
+    }
+    return RMB_OK;
+}
+
+int rmb_batched_results(const rmb_batch_handle* h, rmb_stats* out, void* stream)
+{
+    if (!h || !h->workspace || !out || h->count < 1) return RMB_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
+    std::vector<Ctrl> c(h->count);
+    if (cudaMemcpy(c.data(), static_cast<char*>(h->workspace) + h->ctrl_offset, c.size() * sizeof(Ctrl),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return RMB_ERR_CUDA;
+    int worst = RMB_OK;
+    for (int i = 0; i < h->count; ++i) {
+        std::memset(&out[i], 0, sizeof(rmb_stats));
+        out[i].sweeps = c[i].sweeps;
+        out[i].iters = c[i].iters;
+        out[i].barriers = c[i].barriers;
+        out[i].residual = c[i].residual;
+        out[i].v_shift = c[i].mu;
+        out[i].status = c[i].status != 0 ? c[i].status : c[i].error;
+        out[i].path = -1;
+        if (out[i].status != RMB_OK && worst == RMB_OK) worst = out[i].status;
+    }
+    return worst;
+}
+
+int rmb_batched_graph_create(const rmb_batch_handle* h, void* stream, void** graph_exec)
+{
+    if (!h || !graph_exec || !stream) return RMB_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return RMB_ERR_CUDA;
+    const int st = rmb_batched_run(h, stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (st != RMB_OK || ce != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return st != RMB_OK ? st : RMB_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        return RMB_ERR_CUDA;
+    }
+    *graph_exec = ex;
+    return RMB_OK;
+}
+
+int rmb_batched_graph_launch(void* graph_exec, void* stream)
+{
+    if (!graph_exec) return RMB_ERR_ARG;
+    g_launches++;
+    return cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? RMB_OK
+               : RMB_ERR_CUDA;
+}
+
+int rmb_batched_graph_destroy(void* graph_exec)
+{
+    if (!graph_exec) return RMB_ERR_ARG;
+    return cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec)) == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
+}
+
 
 size_t rmb_workspace_bytes(const rmb_mdp* mdp, const rmb_opts* opts)
 {

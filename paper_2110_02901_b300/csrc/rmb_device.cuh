@@ -140,23 +140,36 @@ struct Ctrl {
     int status, pad;
 };
 
+// The CTAs that solve one MDP: all of the grid (single solves) or a group of it (batched solves).
+struct GroupView {
+    int rank;   // this CTA's index in the group
+    int size;   // CTAs in the group
+};
+
 // Bounded grid-wide barrier, split in two: grid_arrive() publishes this CTA's arrival (thread 0,
 // release add after a CTA barrier and a fence), grid_wait_arrived() spins with acquire loads until
 // every CTA has arrived.  A wait gives up after timeout_ns, or as soon as another CTA reports an
 // error, and then returns false in every thread of the CTA.
-__device__ __forceinline__ void grid_arrive(Ctrl* c, unsigned long long& target, bool skip_arrive)
+__device__ __forceinline__ void grid_arrive(Ctrl* c, unsigned long long& target, bool skip_arrive, int gsize)
 {
     __syncthreads();
+    if (gsize == 1) return;   // a one-CTA group synchronises with the CTA barrier alone
     if (threadIdx.x == 0) {
-        target += gridDim.x;
+        target += gsize;
         __threadfence();
         if (!skip_arrive) red_release_add_u64(&c->bar, 1ull);
     }
 }
 
-__device__ __forceinline__ bool grid_wait_arrived(Ctrl* c, unsigned long long target, int64_t timeout_ns, int site)
+__device__ __forceinline__ bool grid_wait_arrived(Ctrl* c, unsigned long long target, int64_t timeout_ns, int site,
+                                                  int gsize)
 {
     __shared__ int s_ok;
+    if (gsize == 1) {
+        if (threadIdx.x == 0) s_ok = ld_volatile(&c->error) == 0;
+        __syncthreads();
+        return s_ok != 0;
+    }
     if (threadIdx.x == 0) {
         int ok = 1;
         const uint64_t t0 = globaltimer_ns();
