@@ -56,12 +56,17 @@ typedef enum {
 
 enum { RMB_DENSE = 0, RMB_CSR = 1 };
 
+/* Storage of dense transition rows.  RMB_P_F32 rows are used as given.  RMB_P_BF16 / RMB_P_FP8E4M3
+   rows are codes c_rj = p_rj / scale_r (rmb_quantize_rows); the kernels decode them to float32 and
+   divide by the decoded row sum, so the scale cancels and every decoded row is a distribution. */
+enum { RMB_P_F32 = 0, RMB_P_BF16 = 1, RMB_P_FP8E4M3 = 2 };
+
 /* The MDP (Sec. II-A).  All pointers are device pointers. */
 typedef struct {
     int64_t n;               /* number of states, 1 <= n < 2^31 */
     int32_t m;               /* actions per state, >= 1 */
     int32_t format;          /* RMB_DENSE or RMB_CSR */
-    const float *P;          /* RMB_DENSE: [n*m*n] */
+    const void *P;           /* RMB_DENSE: [n*m*n] elements of p_dtype */
     const int64_t *row_ptr;  /* RMB_CSR: [n*m+1] */
     const int32_t *col;      /* RMB_CSR: [nnz] */
     const float *prob;       /* RMB_CSR: [nnz] */
@@ -69,7 +74,8 @@ typedef struct {
     double gamma;            /* discount, 0 < gamma < 1 */
     int32_t k_uniform;       /* RMB_CSR: k > 0 declares row_ptr[r] == r*k for every row (enables
                                 the vectorised row path; checked when validate != 0); 0 = unknown */
-    int32_t reserved;
+    int32_t p_dtype;         /* RMB_DENSE: RMB_P_F32 / RMB_P_BF16 / RMB_P_FP8E4M3 */
+    const float *row_scale;  /* RMB_DENSE coded rows: [n*m] scales (informational; may be NULL) */
 } rmb_mdp;
 
 /* Options of a solve. */
@@ -282,6 +288,26 @@ int rmb_batched_results(const rmb_batch_handle *handle, rmb_stats *out, void *st
 int rmb_batched_graph_create(const rmb_batch_handle *handle, void *stream, void **graph_exec);
 int rmb_batched_graph_launch(void *graph_exec, void *stream);
 int rmb_batched_graph_destroy(void *graph_exec);
+
+/*
+ * Row quantiser: codes[r][j] = round-to-nearest-even(P[r][j] / scale[r]) in p_dtype, with
+ * scale[r] = max_j P[r][j] / F (F = 1 for bf16, 448 = the largest finite e4m3 value for fp8, so
+ * no code saturates; a zero row gets scale 1).  P [rows*cols] float32, codes [rows*cols] 2- or
+ * 1-byte elements, scale [rows]: device.  The low-precision storage of the dense workload.
+ */
+int rmb_quantize_rows(const float *P, int64_t rows, int64_t cols, int32_t p_dtype, void *codes,
+                      float *scale, void *stream);
+
+/*
+ * MB-VI with low-precision transition storage and float32 refinement: first MB-VI on `lowp`
+ * (coded rows) until the sweep residual is <= eps_low (or opts.max_sweeps), then MB-VI sweeps on
+ * `ref` (the same MDP with float32 rows) from those values until the residual is <= opts.eps; the
+ * greedy policy and Q-gap come from the final float32 pass.  lowp and ref must agree in n, m, cost
+ * and gamma.  stats_low / stats_ref (optional) receive each phase's results (then the call waits).
+ */
+int rmb_vi_refined(const rmb_mdp *lowp, const rmb_mdp *ref, const rmb_opts *opts, double eps_low,
+                   float *V_inout, int32_t *pi_out, float *qgap_out, void *workspace,
+                   size_t workspace_bytes, rmb_stats *stats_low, rmb_stats *stats_ref, void *stream);
 
 /* Static text for a status code. */
 const char *rmb_status_string(int status);

@@ -33,6 +33,9 @@ RMB_ERR_TOO_LARGE = -9
 RMB_NOALLOC_SCRATCH_BYTES = 8 << 20
 RMB_DENSE = 0
 RMB_CSR = 1
+RMB_P_F32 = 0
+RMB_P_BF16 = 1
+RMB_P_FP8E4M3 = 2
 RMB_FLAG_INJECT_BARRIER_STALL = 1
 RMB_FLAG_RAW_ROWS = 2
 PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic"}
@@ -43,7 +46,7 @@ class rmb_mdp(ctypes.Structure):
         ("n", ctypes.c_int64), ("m", ctypes.c_int32), ("format", ctypes.c_int32),
         ("P", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p), ("col", ctypes.c_void_p),
         ("prob", ctypes.c_void_p), ("cost", ctypes.c_void_p), ("gamma", ctypes.c_double),
-        ("k_uniform", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("k_uniform", ctypes.c_int32), ("p_dtype", ctypes.c_int32), ("row_scale", ctypes.c_void_p),
     ]
 
 
@@ -158,7 +161,7 @@ class DeviceMDP:
     """An MDP resident in device memory (torch tensors) plus its rmb_mdp descriptor."""
 
     def __init__(self, n, m, gamma, fmt, cost, P=None, row_ptr=None, col=None, prob=None,
-                 k_uniform: int = 0, name: str = ""):
+                 k_uniform: int = 0, name: str = "", p_dtype: int = 0, row_scale=None):
         self.n, self.m, self.gamma, self.fmt, self.name = int(n), int(m), float(gamma), fmt, name
         self.cost, self.P, self.row_ptr, self.col, self.prob = cost, P, row_ptr, col, prob
         self.k_uniform = int(k_uniform)
@@ -168,6 +171,9 @@ class DeviceMDP:
         d.cost = _ptr(cost)
         d.P, d.row_ptr, d.col, d.prob = _ptr(P), _ptr(row_ptr), _ptr(col), _ptr(prob)
         d.k_uniform = self.k_uniform
+        self.p_dtype, self.row_scale = int(p_dtype), row_scale
+        d.p_dtype = self.p_dtype
+        d.row_scale = _ptr(row_scale)
         self.desc = d
 
     @classmethod
@@ -365,6 +371,52 @@ def rmb_fixed_point_grad(mdp: DeviceMDP, pi, V, w, opts: Opts, lam=None, grad_co
            _ptr(grad_logits), _ptr(ws), nb, ctypes.byref(s) if s is not None else None, _stream_handle(stream))
     d = _finish(st, s, "rmb_fixed_point_grad")
     return lam, grad_cost, grad_logits, d
+
+
+def rmb_quantize_rows(P, rows: int, cols: int, p_dtype: int, codes=None, scale=None, stream=None):
+    """Quantise float32 rows to bf16 / fp8-e4m3 codes with per-row scales (see rmb.h)."""
+    import torch
+    _check(P, torch.float32, rows * cols, "P")
+    dt = torch.bfloat16 if p_dtype == RMB_P_BF16 else torch.uint8
+    codes = torch.empty(rows * cols, dtype=dt, device=P.device) if codes is None else codes
+    scale = torch.empty(rows, dtype=torch.float32, device=P.device) if scale is None else scale
+    f = lib().rmb_quantize_rows
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    st = f(_ptr(P), int(rows), int(cols), int(p_dtype), _ptr(codes), _ptr(scale), _stream_handle(stream))
+    if st != RMB_OK:
+        raise RmbError(st, "rmb_quantize_rows")
+    return codes, scale
+
+
+def dense_lowp(dm: DeviceMDP, p_dtype: int, stream=None) -> DeviceMDP:
+    """The same dense MDP with its rows stored as bf16 / fp8-e4m3 codes (quantised on the device)."""
+    rows = dm.n * dm.m
+    codes, scale = rmb_quantize_rows(dm.P.reshape(-1), rows, dm.n, p_dtype, stream=stream)
+    return DeviceMDP(dm.n, dm.m, dm.gamma, "dense", dm.cost, P=codes, p_dtype=p_dtype, row_scale=scale,
+                     name=f"{dm.name}-{'bf16' if p_dtype == RMB_P_BF16 else 'fp8'}")
+
+
+def rmb_vi_refined(lowp: DeviceMDP, ref: DeviceMDP, opts: Opts, eps_low: float, V, pi=None, qgap=None, ws=None,
+                   stream=None):
+    """Low-precision MB-VI to eps_low, then float32 refinement sweeps to opts.eps (see rmb.h).
+    Returns (stats of the low-precision phase, stats of the refinement phase)."""
+    import torch
+    _check(V, torch.float32, ref.n, "V")
+    ws = workspace(ref, opts) if ws is None else ws
+    f = lib().rmb_vi_refined
+    f.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.POINTER(rmb_mdp), ctypes.POINTER(rmb_opts), ctypes.c_double,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                  ctypes.POINTER(rmb_stats), ctypes.POINTER(rmb_stats), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    o = opts.desc()
+    s1, s2 = rmb_stats(), rmb_stats()
+    st = f(ctypes.byref(lowp.desc), ctypes.byref(ref.desc), ctypes.byref(o), float(eps_low), _ptr(V), _ptr(pi),
+           _ptr(qgap), _ptr(ws), ws.numel(), ctypes.byref(s1), ctypes.byref(s2), _stream_handle(stream))
+    if st not in (RMB_OK, RMB_ERR_NOT_CONVERGED):
+        raise RmbError(st, "rmb_vi_refined")
+    return s1.as_dict(), s2.as_dict()
 
 
 def rmb_permutation(n: int, seed: int, sweep: int, out=None, stream=None):

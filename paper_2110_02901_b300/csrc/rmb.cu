@@ -20,6 +20,8 @@
 // - (1 - gamma) mu.  mu moves (and every d with it) only between sweeps, when the midpoint of the
 // values drifts by more than a quarter of their spread.
 
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -49,7 +51,8 @@ constexpr int kDenseMaxStage = 40960;     // floats of V staged at once (160 KB 
 struct KP {
     // problem
     int n, m, k, path;
-    const float* P;
+    int p_dtype;            // dense: RMB_P_F32 / RMB_P_BF16 / RMB_P_FP8E4M3
+    const void* P;
     const int64_t* row_ptr;
     const int32_t* col;
     const float* prob;
@@ -465,6 +468,7 @@ struct DenseSmem {
     uint32_t phase;
     int ok;
     float red[kDenseThreads / 32][kDenseMB];
+    float red2[kDenseThreads / 32][kDenseMB];
     float q[kDenseMaxM];
     int perm[32];
 };
@@ -511,23 +515,77 @@ __device__ __forceinline__ bool stage_values(const KP& p, DenseSmem& sm, float* 
     return ok;
 }
 
-template <int KIND, bool VEC>
+// Dense row elements: float32, or bf16 / fp8-e4m3 codes.  Coded rows are renormalised by the sum of
+// their decoded entries (the per-row scale cancels), so a decoded row is an exact distribution and
+// gamma * row sum never exceeds gamma.
+template <int DT>
+struct Elem {
+    static constexpr int bytes = DT == RMB_P_F32 ? 4 : (DT == RMB_P_BF16 ? 2 : 1);
+    static constexpr int per16 = 16 / bytes;   // elements in one 16-byte load
+};
+
+template <int DT>
+__device__ __forceinline__ void decode16(const uint4 w, float* d)
+{
+    if (DT == RMB_P_F32) {
+        d[0] = __uint_as_float(w.x);
+        d[1] = __uint_as_float(w.y);
+        d[2] = __uint_as_float(w.z);
+        d[3] = __uint_as_float(w.w);
+    } else if (DT == RMB_P_BF16) {
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            d[2 * i] = __uint_as_float(u[i] << 16);
+            d[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
+        }
+    } else {
+        const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u[i] & 0xffffu), __NV_E4M3);
+            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u[i] >> 16), __NV_E4M3);
+            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+            d[4 * i] = a.x;
+            d[4 * i + 1] = a.y;
+            d[4 * i + 2] = b.x;
+            d[4 * i + 3] = b.y;
+        }
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ float decode1(const unsigned char* row, int64_t j)
+{
+    if (DT == RMB_P_F32) return __ldcs(reinterpret_cast<const float*>(row) + j);
+    if (DT == RMB_P_BF16) return __uint_as_float((uint32_t)__ldcs(reinterpret_cast<const unsigned short*>(row) + j) << 16);
+    const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)__ldcs(reinterpret_cast<const unsigned char*>(row) + j),
+                                                __NV_E4M3);
+    return __half2float(*reinterpret_cast<const __half*>(&h));
+}
+
+template <int KIND, int DT, bool VEC>
 __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole, const float* A, int s,
                             int pi_s, bool* ok)
 {
+    constexpr int EB = Elem<DT>::bytes;
+    constexpr int E = Elem<DT>::per16;
+    constexpr bool NORM = DT != RMB_P_F32;
     const int n = p.n;
     const int nrows = pi_s >= 0 ? 1 : p.m;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nw = blockDim.x >> 5;
+    const unsigned char* P = static_cast<const unsigned char*>(p.P);
     for (int a0 = 0; a0 < nrows; a0 += kDenseMB) {
-        float acc[kDenseMB];
+        float acc[kDenseMB], sum[kDenseMB];
 #pragma unroll
-        for (int u = 0; u < kDenseMB; ++u) acc[u] = 0.f;
-        const float* rows[kDenseMB];
+        for (int u = 0; u < kDenseMB; ++u) acc[u] = sum[u] = 0.f;
+        const unsigned char* rows[kDenseMB];
 #pragma unroll
         for (int u = 0; u < kDenseMB; ++u) {
             const int a = pi_s >= 0 ? pi_s : min(a0 + u, p.m - 1);
-            rows[u] = p.P + ((int64_t)s * p.m + a) * (int64_t)n;
+            rows[u] = P + ((int64_t)s * p.m + a) * (int64_t)n * EB;
         }
         for (int c0 = 0; c0 < n; c0 += p.stage) {
             const int clen = min(p.stage, n - c0);
@@ -536,17 +594,27 @@ __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole
                 if (!stage_values(p, sm, stage, A + c0, (clen + 3) & ~3)) { *ok = false; return Best{kInf, 0, kInf}; }
             }
             if (VEC) {
-                const float4* st4 = reinterpret_cast<const float4*>(stage);
-                for (int j4 = tid; j4 < (clen >> 2); j4 += blockDim.x) {
-                    const float4 v = st4[j4];
+                for (int jv = tid; jv < clen / E; jv += blockDim.x) {
+                    float v[E];
+#pragma unroll
+                    for (int q = 0; q < E / 4; ++q) {
+                        const float4 f = reinterpret_cast<const float4*>(stage)[jv * (E / 4) + q];
+                        v[4 * q] = f.x;
+                        v[4 * q + 1] = f.y;
+                        v[4 * q + 2] = f.z;
+                        v[4 * q + 3] = f.w;
+                    }
 #pragma unroll
                     for (int u = 0; u < kDenseMB; ++u) {
                         if (a0 + u < nrows) {
-                            const float4 pr = __ldcs(reinterpret_cast<const float4*>(rows[u] + c0) + j4);
-                            acc[u] = fmaf(pr.x, v.x, acc[u]);
-                            acc[u] = fmaf(pr.y, v.y, acc[u]);
-                            acc[u] = fmaf(pr.z, v.z, acc[u]);
-                            acc[u] = fmaf(pr.w, v.w, acc[u]);
+                            const uint4 w = __ldcs(reinterpret_cast<const uint4*>(rows[u] + (int64_t)c0 * EB) + jv);
+                            float d[E];
+                            decode16<DT>(w, d);
+#pragma unroll
+                            for (int e = 0; e < E; ++e) {
+                                acc[u] = fmaf(d[e], v[e], acc[u]);
+                                if (NORM) sum[u] += d[e];
+                            }
                         }
                     }
                 }
@@ -554,21 +622,36 @@ __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole
                 for (int j = tid; j < clen; j += blockDim.x) {
                     const float v = stage[j];
 #pragma unroll
-                    for (int u = 0; u < kDenseMB; ++u)
-                        if (a0 + u < nrows) acc[u] = fmaf(__ldcs(rows[u] + c0 + j), v, acc[u]);
+                    for (int u = 0; u < kDenseMB; ++u) {
+                        if (a0 + u < nrows) {
+                            const float d = decode1<DT>(rows[u], c0 + j);
+                            acc[u] = fmaf(d, v, acc[u]);
+                            if (NORM) sum[u] += d;
+                        }
+                    }
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < kDenseMB; ++u) {
-            float x = acc[u];
-            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            if (lane == 0) sm.red[wid][u] = x;
+            float x = acc[u], y = sum[u];
+            for (int off = 16; off > 0; off >>= 1) {
+                x += __shfl_xor_sync(0xffffffffu, x, off);
+                if (NORM) y += __shfl_xor_sync(0xffffffffu, y, off);
+            }
+            if (lane == 0) {
+                sm.red[wid][u] = x;
+                sm.red2[wid][u] = y;
+            }
         }
         __syncthreads();
         if (tid < kDenseMB && a0 + tid < nrows) {
-            float tot = 0.f;
-            for (int w = 0; w < nw; ++w) tot += sm.red[w][tid];
+            float tot = 0.f, tsum = 0.f;
+            for (int w = 0; w < nw; ++w) {
+                tot += sm.red[w][tid];
+                tsum += sm.red2[w][tid];
+            }
+            if (NORM) tot = tsum > 0.f ? tot / tsum : 0.f;
             const int a = pi_s >= 0 ? pi_s : a0 + tid;
             const float c = __ldg(p.cost + (int64_t)s * p.m + a);
             sm.q[a0 + tid] = (c == kInf) ? kInf : fmaf(p.gamma, tot, c);
@@ -585,7 +668,7 @@ __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole
     return best;
 }
 
-template <int KIND, bool VEC>
+template <int KIND, int DT, bool VEC>
 __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, float* stage, const float* A, float* B,
                             int pos0, int len, const PermKey* K, int32_t* Sout, float* Wout, const Centre& C,
                             Acc& acc, bool* perm_ok)
@@ -611,7 +694,7 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
             const int pi_s = (KIND == K_POLICY)
                                  ? (int)min((uint32_t)ld_l2(p.pi_in ? p.pi_in + s : p.pi + s), (uint32_t)(p.m - 1))
                                  : -1;
-            const Best r = dense_state<KIND, VEC>(p, sm, stage, whole, A, s, pi_s, &ok);
+            const Best r = dense_state<KIND, DT, VEC>(p, sm, stage, whole, A, s, pi_s, &ok);
             if (!ok) return false;
             if (threadIdx.x == 0)
                 state_epilogue<KIND>(p, r, s, me + (j0 + jj) * G, A, B, Sout, Wout, C, acc);
@@ -725,9 +808,11 @@ struct Runner {
                           Acc& acc)
     {
         if (PATH == PATH_DENSE) {
-            if (p.n % 4 == 0 && (((uintptr_t)p.P) & 15) == 0)
-                return dense_batch<KIND, true>(p, gv, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
-            return dense_batch<KIND, false>(p, gv, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+            // dense kernels are instantiated per storage type: NCA carries the element type
+            constexpr int DT = NCA;
+            const bool vec = (((uintptr_t)p.P) & 15) == 0 && p.n % Elem<DT>::per16 == 0;
+            if (vec) return dense_batch<KIND, DT, true>(p, gv, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+            return dense_batch<KIND, DT, false>(p, gv, *dsm, stage, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
         } else {
             const int lps = (KIND == K_POLICY) ? p.lps_one : p.lps_all;
             if (PATH == PATH_CSR_VEC && KIND == K_POLICY && NCO > 0) {
@@ -1011,12 +1096,14 @@ __global__ void __launch_bounds__(kCsrThreads, 2) rmb_csr_gen_kernel(KP p)
     R.run();
 }
 
-__global__ void __launch_bounds__(kDenseThreads, 3) rmb_dense_kernel(KP p)
+// Dense rows; DT = element type of P (RMB_P_F32 / RMB_P_BF16 / RMB_P_FP8E4M3).
+template <int DT>
+__global__ void __launch_bounds__(kDenseThreads, 2) rmb_dense_kernel(KP p)
 {
     __shared__ RedSmem rs;
     __shared__ __align__(16) DenseSmem dsm;
     extern __shared__ __align__(128) float stage[];
-    Runner<PATH_DENSE> R(p, rs, &dsm, stage, GroupView{(int)blockIdx.x, (int)gridDim.x});
+    Runner<PATH_DENSE, DT> R(p, rs, &dsm, stage, GroupView{(int)blockIdx.x, (int)gridDim.x});
     R.run();
 }
 
@@ -1185,6 +1272,30 @@ __global__ void rmb_grad_kernel(int n, int m, int k, float gamma, const int32_t*
     }
 }
 
+// Row quantiser (low-precision storage of dense rows): one warp per row.
+__global__ void rmb_quantize_kernel(const float* __restrict__ P, int64_t rows, int64_t cols, int dt,
+                                    void* __restrict__ codes, float* __restrict__ scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = warp; r < rows; r += nw) {
+        const float* row = P + r * cols;
+        float mx = 0.f;
+        for (int64_t j = lane; j < cols; j += 32) mx = fmaxf(mx, row[j]);
+        for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        const float sc = mx > 0.f ? (dt == RMB_P_FP8E4M3 ? mx / 448.f : mx) : 1.f;
+        if (lane == 0 && scale) scale[r] = sc;
+        if (dt == RMB_P_BF16) {
+            __nv_bfloat16* out = static_cast<__nv_bfloat16*>(codes) + r * cols;
+            for (int64_t j = lane; j < cols; j += 32) out[j] = __float2bfloat16_rn(row[j] / sc);
+        } else {
+            __nv_fp8_storage_t* out = static_cast<__nv_fp8_storage_t*>(codes) + r * cols;
+            for (int64_t j = lane; j < cols; j += 32) out[j] = __nv_cvt_float_to_fp8(row[j] / sc, __NV_SATFINITE, __NV_E4M3);
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Permutation and validation kernels.
 // ------------------------------------------------------------------------------------------------
@@ -1200,8 +1311,8 @@ __global__ void rmb_perm_kernel(uint32_t n, uint32_t h, uint32_t k0, uint32_t k1
 }
 
 struct VP {
-    int n, m, k, fmt;
-    const float* P;
+    int n, m, k, fmt, p_dtype;
+    const void* P;
     const int64_t* row_ptr;
     const int32_t* col;
     const float* prob;
@@ -1233,15 +1344,22 @@ __global__ void rmb_validate_kernel(VP v)
                 sum += pr;
             }
         } else {
-            const float* row = v.P + r * (size_t)v.n;
+            const unsigned char* row = static_cast<const unsigned char*>(v.P) +
+                                       r * (size_t)v.n * (v.p_dtype == RMB_P_F32 ? 4 : (v.p_dtype == RMB_P_BF16 ? 2 : 1));
             for (int j = lane; j < v.n; j += 32) {
-                const float pr = row[j];
-                if (!(pr >= 0.f && pr <= 1.f)) bad = true;
+                float pr;
+                if (v.p_dtype == RMB_P_BF16) pr = decode1<RMB_P_BF16>(row, j);
+                else if (v.p_dtype == RMB_P_FP8E4M3) pr = decode1<RMB_P_FP8E4M3>(row, j);
+                else pr = decode1<RMB_P_F32>(row, j);
+                // coded rows only need to be finite and non-negative (they are renormalised)
+                if (!(pr >= 0.f && (v.p_dtype != RMB_P_F32 ? pr <= 3.4e38f : pr <= 1.f))) bad = true;
                 sum += pr;
             }
         }
         for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
-        if (admissible && !(fabsf(sum - 1.f) <= 1e-4f)) bad = true;
+        if (admissible && v.fmt == RMB_CSR && !(fabsf(sum - 1.f) <= 1e-4f)) bad = true;
+        if (admissible && v.fmt == RMB_DENSE && v.p_dtype == RMB_P_F32 && !(fabsf(sum - 1.f) <= 1e-4f)) bad = true;
+        if (admissible && v.fmt == RMB_DENSE && v.p_dtype != RMB_P_F32 && !(sum > 0.f)) bad = true;
     }
     // every state needs one admissible action
     for (size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x; s < (size_t)v.n;
@@ -1342,6 +1460,7 @@ int check_mdp(const rmb_mdp* M)
     if (M->format == RMB_DENSE) {
         if (!M->P) return RMB_ERR_ARG;
         if (M->m > kDenseMaxM) return RMB_ERR_UNSUPPORTED;
+        if (M->p_dtype < RMB_P_F32 || M->p_dtype > RMB_P_FP8E4M3) return RMB_ERR_ARG;
     } else if (M->format == RMB_CSR) {
         if (!M->row_ptr || !M->col || !M->prob) return RMB_ERR_ARG;
         if (M->k_uniform < 0) return RMB_ERR_ARG;
@@ -1408,6 +1527,7 @@ int launch_validate(const rmb_mdp* M, int* err, cudaStream_t st, int sms)
     v.m = M->m;
     v.k = M->format == RMB_CSR ? M->k_uniform : 0;
     v.fmt = M->format;
+    v.p_dtype = M->format == RMB_DENSE ? M->p_dtype : RMB_P_F32;
     v.P = M->P;
     v.row_ptr = M->row_ptr;
     v.col = M->col;
@@ -1428,6 +1548,7 @@ int fill_kp(int mode, const rmb_mdp* M, const rmb_opts* O, int64_t b, char* ws, 
     p.m = M->m;
     p.k = M->format == RMB_CSR ? M->k_uniform : 0;
     p.P = M->P;
+    p.p_dtype = M->format == RMB_DENSE ? M->p_dtype : RMB_P_F32;
     p.row_ptr = M->row_ptr;
     p.col = M->col;
     p.prob = M->prob;
@@ -1526,19 +1647,21 @@ int solve(const Call& q)
     int threads, per_sm;
     size_t smem = 0;
     if (path == PATH_DENSE) {
-        fn = reinterpret_cast<const void*>(rmb_dense_kernel);
+        fn = p.p_dtype == RMB_P_BF16      ? reinterpret_cast<const void*>(rmb_dense_kernel<RMB_P_BF16>)
+             : p.p_dtype == RMB_P_FP8E4M3 ? reinterpret_cast<const void*>(rmb_dense_kernel<RMB_P_FP8E4M3>)
+                                          : reinterpret_cast<const void*>(rmb_dense_kernel<RMB_P_F32>);
         threads = kDenseThreads;
         int max_stage = kDenseMaxStage;
         if (const char* e = std::getenv("RMB_DENSE_STAGE")) {   // tuning / test knob: floats staged at once
             const int v = std::atoi(e);
-            if (v >= 4 && v <= kDenseMaxStage) max_stage = v & ~3;
+            if (v >= 16 && v <= kDenseMaxStage) max_stage = v & ~15;
         }
         p.stage = M->n <= max_stage ? (int)((M->n + 3) & ~3LL) : max_stage;
         smem = (size_t)p.stage * 4;
-        if (cudaFuncSetAttribute(rmb_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return RMB_ERR_CUDA;
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, rmb_dense_kernel, threads, smem) != cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess)
             return RMB_ERR_CUDA;
         per_sm = occ < 2 ? occ : 2;
     } else {
@@ -2164,6 +2287,44 @@ int rmb_fixed_point_grad(const rmb_mdp* mdp, const int32_t* pi, const float* V, 
     }
     if (stats && cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
     return st;
+}
+
+int rmb_quantize_rows(const float* P, int64_t rows, int64_t cols, int32_t p_dtype, void* codes, float* scale,
+                      void* stream)
+{
+    if (!P || !codes || rows < 1 || cols < 1) return RMB_ERR_ARG;
+    if (p_dtype != RMB_P_BF16 && p_dtype != RMB_P_FP8E4M3) return RMB_ERR_ARG;
+    DevInfo* D = nullptr;
+    int st = dev_info(&D);
+    if (st) return st;
+    const int blocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)D->sms * 16);
+    rmb_quantize_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(P, rows, cols, p_dtype, codes, scale);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
+}
+
+int rmb_vi_refined(const rmb_mdp* lowp, const rmb_mdp* ref, const rmb_opts* opts, double eps_low, float* V_inout,
+                   int32_t* pi_out, float* qgap_out, void* workspace, size_t workspace_bytes, rmb_stats* stats_low,
+                   rmb_stats* stats_ref, void* stream)
+{
+    int st = check_mdp(lowp);
+    if (st) return st;
+    if ((st = check_mdp(ref))) return st;
+    if (!opts || !(eps_low >= 0.0) || std::isinf(eps_low)) return RMB_ERR_ARG;
+    if (lowp->n != ref->n || lowp->m != ref->m || lowp->gamma != ref->gamma || lowp->cost != ref->cost)
+        return RMB_ERR_ARG;
+    rmb_opts o1 = *opts;
+    o1.eps = eps_low;
+    o1.trace = nullptr;
+    Call q1{MODE_VI, lowp, &o1, V_inout, V_inout, nullptr, nullptr, nullptr, nullptr,
+            workspace, workspace_bytes, stats_low, static_cast<cudaStream_t>(stream)};
+    st = solve(q1);
+    if (st != RMB_OK && st != RMB_ERR_NOT_CONVERGED) return st;
+    rmb_opts o2 = *opts;
+    o2.trace = nullptr;
+    Call q2{MODE_VI, ref, &o2, V_inout, V_inout, nullptr, pi_out, qgap_out, nullptr,
+            workspace, workspace_bytes, stats_ref, static_cast<cudaStream_t>(stream)};
+    return solve(q2);
 }
 
 const char* rmb_status_string(int status)

@@ -49,9 +49,10 @@ def test_struct_layouts_match_header():
 #include <stddef.h>
 #include "rmb.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rmb_mdp), sizeof(rmb_opts), sizeof(rmb_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rmb_mdp), sizeof(rmb_opts), sizeof(rmb_stats),
          offsetof(rmb_mdp, gamma), offsetof(rmb_mdp, k_uniform), offsetof(rmb_opts, trace),
-         offsetof(rmb_stats, ms), offsetof(rmb_opts, flags));
+         offsetof(rmb_stats, ms), offsetof(rmb_opts, flags), offsetof(rmb_mdp, row_scale),
+         sizeof(rmb_batch_item), sizeof(rmb_batch_handle), sizeof(rmb_batch_plan_item));
   return 0;
 }'''
     d = tempfile.mkdtemp()
@@ -62,7 +63,9 @@ int main(void) {
     vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     mine = [ctypes.sizeof(rmb.rmb_mdp), ctypes.sizeof(rmb.rmb_opts), ctypes.sizeof(rmb.rmb_stats),
             rmb.rmb_mdp.gamma.offset, rmb.rmb_mdp.k_uniform.offset, rmb.rmb_opts.trace.offset,
-            rmb.rmb_stats.ms.offset, rmb.rmb_opts.flags.offset]
+            rmb.rmb_stats.ms.offset, rmb.rmb_opts.flags.offset, rmb.rmb_mdp.row_scale.offset,
+            ctypes.sizeof(rmb.rmb_batch_item), ctypes.sizeof(rmb.rmb_batch_handle),
+            ctypes.sizeof(rmb.rmb_batch_plan_item)]
     assert vals == mine
 
 

@@ -1,0 +1,114 @@
+"""Low-precision dense transitions (bf16 / fp8-e4m3 codes with per-row scales) and float32 refinement.
+
+* the device quantiser equals torch's CPU conversion of P / scale bit for bit;
+* a low-precision solve equals the FP64 oracle run on the decoded, renormalised rows (that is the
+  operator the kernel applies) within the FP32 value tolerance;
+* the refined solve (low precision, then float32 sweeps) equals the oracle on the float32 problem;
+* the error of the unrefined low-precision solution against the float32 problem is reported.
+"""
+import numpy as np
+import pytest
+
+import mdpgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2110_02901_b300 as rmb  # noqa: E402
+from paper_2110_02901_b300 import build as rbuild  # noqa: E402
+
+RTOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    rbuild.build()
+    rmb.lib()
+
+
+def close(a, b, tol=RTOL):
+    a = np.asarray(a, np.float64)
+    scale = max(1.0, float(np.abs(b).max()))
+    err = float(np.abs(a - b).max())
+    assert err <= tol * scale, f"{err:.3e} > {tol:.0e} * {scale:.3e}"
+    return err
+
+
+def cpu_codes(P2d, dt):
+    """Reference quantisation with torch on the CPU (a library conversion, not the CUDA path)."""
+    P = torch.from_numpy(P2d)
+    mx = P.max(dim=1).values
+    if dt == rmb.RMB_P_FP8E4M3:
+        sc = torch.where(mx > 0, mx / 448.0, torch.ones_like(mx))
+        codes = (P / sc[:, None]).to(torch.float8_e4m3fn)
+    else:
+        sc = torch.where(mx > 0, mx, torch.ones_like(mx))
+        codes = (P / sc[:, None]).to(torch.bfloat16)
+    return codes, sc
+
+
+def decoded_mdp(mdp, codes):
+    """The MDP the low-precision kernel applies: decoded codes, each row divided by its sum."""
+    d = codes.to(torch.float64).numpy()
+    d = d / d.sum(axis=1, keepdims=True)
+    out = mdpgen.MDP(n=mdp.n, m=mdp.m, gamma=mdp.gamma, fmt="dense", cost=mdp.cost,
+                     P=d.astype(np.float32).reshape(mdp.n, mdp.m, mdp.n))
+    return out
+
+
+@pytest.mark.parametrize("dt", [rmb.RMB_P_BF16, rmb.RMB_P_FP8E4M3])
+def test_quantiser_matches_cpu_conversion(dt):
+    mdp = mdpgen.dense_dirichlet(1024, 4, alpha=0.1, gamma=0.999, seed=3, cost_dist="normal")
+    P2 = mdp.P.reshape(-1, mdp.n)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    codes, scale = rmb.rmb_quantize_rows(dm.P.reshape(-1), P2.shape[0], P2.shape[1], dt)
+    want, sc = cpu_codes(P2, dt)
+    assert torch.equal(scale.cpu(), sc)
+    if dt == rmb.RMB_P_FP8E4M3:
+        assert torch.equal(codes.cpu().reshape(P2.shape), want.view(torch.uint8))
+    else:
+        assert torch.equal(codes.cpu().reshape(P2.shape), want)
+
+
+@pytest.mark.parametrize("dt", [rmb.RMB_P_BF16, rmb.RMB_P_FP8E4M3])
+@pytest.mark.parametrize("n,m,b", [(1024, 16, 256), (512, 8, 512), (400, 3, 33)])
+def test_lowp_trajectory_matches_oracle_on_decoded_rows(dt, n, m, b):
+    mdp = mdpgen.dense_dirichlet(n, m, alpha=0.1, gamma=0.999, seed=n + m, cost_dist="normal")
+    dm = rmb.DeviceMDP.from_host(mdp)
+    lp = rmb.dense_lowp(dm, dt)
+    codes, _ = cpu_codes(mdp.P.reshape(-1, n), dt)
+    dec = decoded_mdp(mdp, codes)
+    V0 = mdpgen.random_values(n, seed=1)
+    ref = oracle.mbvi(dec, b, seed=9, eps=0.0, max_sweeps=4, V0=V0, traj=True)
+    V = torch.from_numpy(V0).cuda()
+    st = rmb.rmb_vi(lp, rmb.Opts(batch=b, seed=9, eps=0.0, max_sweeps=4), V)
+    assert st["sweeps"] == 4 and st["path"] == "dense"
+    close(V.cpu().numpy(), ref["traj"][3])
+
+
+@pytest.mark.parametrize("dt", [rmb.RMB_P_BF16, rmb.RMB_P_FP8E4M3])
+def test_converged_lowp_and_refined_solutions(dt):
+    n, m, b = 512, 8, 64
+    mdp = mdpgen.dense_dirichlet(n, m, alpha=0.1, gamma=0.99, seed=7, cost_dist="normal")
+    dm = rmb.DeviceMDP.from_host(mdp)
+    lp = rmb.dense_lowp(dm, dt)
+    codes, _ = cpu_codes(mdp.P.reshape(-1, n), dt)
+    dec = decoded_mdp(mdp, codes)
+    ref_lp = oracle.mbvi(dec, b, seed=5, eps=1e-7, max_sweeps=100000)
+    ref = oracle.mbvi(mdp, b, seed=5, eps=1e-7, max_sweeps=100000)
+    V = torch.zeros(n, dtype=torch.float32, device="cuda")
+    st = rmb.rmb_vi(lp, rmb.Opts(batch=b, seed=5, eps=1e-7, max_sweeps=100000), V)
+    assert st["status"] == rmb.RMB_OK
+    close(V.cpu().numpy(), ref_lp["V"])
+    lowp_err = float(np.abs(V.cpu().numpy() - ref["V"]).max()) / float(np.abs(ref["V"]).max())
+    V2 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(n, dtype=torch.int32, device="cuda")
+    s1, s2 = rmb.rmb_vi_refined(lp, dm, rmb.Opts(batch=b, seed=5, eps=1e-7, max_sweeps=100000), 1e-7, V2, pi)
+    assert s2["status"] == rmb.RMB_OK
+    ref_err = close(V2.cpu().numpy(), ref["V"]) / max(1.0, float(np.abs(ref["V"]).max()))
+    print(f"dtype={dt}: relative error vs float32 problem, low precision {lowp_err:.2e}, refined {ref_err:.2e}, "
+          f"sweeps {s1['sweeps']} + {s2['sweeps']}")
+    assert ref_err < lowp_err
