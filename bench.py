@@ -221,6 +221,11 @@ def main():
     ap.add_argument("--n-log2", type=int, default=20, help="states = 2^n_log2 (profiling of smaller cases)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="SWEEPS",
                     help="profiling mode: one MB-VI solve of exactly SWEEPS sweeps (no bench line)")
+    ap.add_argument("--workload", default="csr", choices=["csr", "dense500", "dense16k", "batched", "adjoint"],
+                    help="csr: the headline line (default); the others measure the remaining workloads")
+    ap.add_argument("--full", action="store_true", help="dense16k: also time full gamma=0.999 solves at n=16384")
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"],
+                    help="dense16k --profile-case: storage type of P")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -228,6 +233,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.workload != "csr":
+        return run_workload(args, world, rank, local)
 
     import torch
     import paper_2110_02901_b300 as rmb
@@ -373,6 +380,258 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# The other workloads (one JSON line each; not the headline line).
+# ------------------------------------------------------------------------------------------------
+def _line(metric, value, unit, ms, args, world, config, **kw):
+    d = {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+         "data": "synthetic", "config": config}
+    d.update(kw)
+    return d
+
+
+def _timed(fn, steps, stream):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs = [fn() for _ in range(steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, outs
+
+
+def run_workload(args, world, rank, local):
+    import torch
+    import paper_2110_02901_b300 as rmb
+    from paper_2110_02901_b300 import build as rbuild
+    rbuild.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    hbm, peak_kind = peaks()
+    l0 = rmb.rmb_kernel_launches()
+    with ClockSampler(local) as clk:
+        line = {"dense500": _dense500, "dense16k": _dense16k, "batched": _batched, "adjoint": _adjoint}[
+            args.workload](args, world, rmb, torch, stream, hbm, peak_kind)
+    line["clocks"] = clk.summary()
+    line["gpu_launches_total"] = rmb.rmb_kernel_launches() - l0
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def _dense500(args, world, rmb, torch, stream, hbm, peak_kind):
+    """Dense n=500, m=4, Dirichlet(1), gamma=0.95, b=50: MB-VI to 1e-6 (latency-bound: P is 4 MB)."""
+    import oracle
+    mdp = mdpgen.config1()
+    dm = rmb.DeviceMDP.from_host(mdp)
+    o = rmb.Opts(batch=50, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=100000, validate=False)
+    ws = rmb.workspace(dm, o)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
+
+    def step():
+        V.zero_()
+        return rmb.rmb_vi(dm, o, V, pi, None, ws=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    ms, outs = _timed(step, args.steps, stream)
+    sw = outs[-1]["sweeps"]
+    t0 = time.perf_counter()
+    ref = oracle.mbvi(mdp, 50, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=100000)
+    ct = time.perf_counter() - t0
+    err = float(np.abs(V.cpu().numpy() - ref["V"]).max())
+    bytes_launch = (sw + 1) * mdp.n * mdp.m * mdp.n * 4
+    ach = bytes_launch / (outs[-1]["ms"] / 1e3) / 1e9
+    return _line(METRIC, mdp.n * sw / (ms / 1e3), "Bellman backups/s", ms, args, world,
+                 {"workload": "dense-mdp n=500 m=4 dirichlet(1) c~U[0,1] gamma=0.95; MB-VI b=50 from V=0 to 1e-6",
+                  "sweeps": sw, "barriers_per_solve": outs[-1]["barriers"], "time_to_eps_ms": ms,
+                  "max_abs_err_vs_oracle": err, "l2": "P is 4 MB: L2-resident by design (latency-bound workload)"},
+                 roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "traffic": None, "kernel": "rmb_dense_kernel<f32>", "peak_kind": peak_kind,
+                           "note": "P is L2-resident; the bound is the per-batch barrier latency (10 batches/sweep)"},
+                 cpu_baseline={"value": mdp.n * ref["sweeps"] / ct, "unit": "Bellman backups/s",
+                               "cores": oracle.num_threads(), "kind": "oracle",
+                               "sample": f"full solve, {ref['sweeps']} sweeps, {ct:.2f} s"})
+
+
+def _dense16k(args, world, rmb, torch, stream, hbm, peak_kind):
+    """Dense n=16384, m=16, Dirichlet(0.1), c~N(0,1), gamma=0.999: sweep throughput per storage type and
+    b; converged error per storage type on the same recipe at n=2048 against the exact optimum."""
+    from oracle import exact
+    if args.profile_case:
+        # profiling mode: one solve of exactly profile_case sweeps at n = 2^n_log2 (default 2^20 is
+        # reduced to 2^12 here), b = n/4, storage --storage
+        n = 1 << (args.n_log2 if args.n_log2 != 20 else 12)
+        P, cost = mdpgen.dense_dirichlet_device(n, 16, 0.1, 0.999, seed=3)
+        dm = rmb.DeviceMDP(n, 16, 0.999, "dense", cost, P=P.reshape(-1))
+        if args.storage != "f32":
+            dm = rmb.dense_lowp(dm, rmb.RMB_P_BF16 if args.storage == "bf16" else rmb.RMB_P_FP8E4M3)
+        V = torch.zeros(n, dtype=torch.float32, device="cuda")
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=n // 4, eps=0.0, max_sweeps=args.profile_case, validate=False), V)
+        eb = {"f32": 4, "bf16": 2, "fp8": 1}[args.storage]
+        gb = st["sweeps"] * n * 16 * n * eb / 1e9
+        return {"profile_case": True, "n": n, "storage": args.storage, "sweeps": st["sweeps"], "ms": st["ms"],
+                "gbs": gb / (st["ms"] / 1e3)}
+    n, m = 16384, 16
+    P, cost = mdpgen.dense_dirichlet_device(n, m, 0.1, 0.999, seed=3)
+    d32 = rmb.DeviceMDP(n, m, 0.999, "dense", cost, P=P.reshape(-1), name="dense16k")
+    forms = {"f32": d32, "bf16": rmb.dense_lowp(d32, rmb.RMB_P_BF16), "fp8": rmb.dense_lowp(d32, rmb.RMB_P_FP8E4M3)}
+    ebytes = {"f32": 4, "bf16": 2, "fp8": 1}
+    thr = []
+    V = torch.zeros(n, dtype=torch.float32, device="cuda")
+    for name, dm in forms.items():
+        for b in (256, 4096):
+            o = rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=20, validate=False)
+            ws = rmb.workspace(dm, o)
+            st = None
+            for _ in range(2):
+                V.zero_()
+                st = rmb.rmb_vi(dm, o, V, None, None, ws=ws, stream=stream)
+            per = st["ms"] / st["sweeps"]
+            gb = n * m * n * ebytes[name] / 1e9
+            thr.append({"storage": name, "b": b, "ms_per_sweep": per, "p_stream_gbs": gb / (per / 1e3),
+                        "hbm_frac": gb / (per / 1e3) / hbm, "backups_per_s": n / (per / 1e3)})
+    full = {}
+    if args.full:
+        for name in ("f32", "fp8", "bf16"):
+            o = rmb.Opts(batch=4096, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=200000, validate=False)
+            V.zero_()
+            if name == "f32":
+                st = rmb.rmb_vi(forms["f32"], o, V, stream=stream)
+                full[name] = {"time_to_eps_ms": st["ms"], "sweeps": st["sweeps"]}
+            else:
+                s1, s2 = rmb.rmb_vi_refined(forms[name], forms["f32"], o, EPS, V)
+                full[name + "+f32 refinement"] = {"time_to_eps_ms": s1["ms"] + s2["ms"],
+                                                  "sweeps": [s1["sweeps"], s2["sweeps"]]}
+    del forms, d32, P
+    torch.cuda.empty_cache()
+    # converged error per storage type, same recipe at n = 2048, against the exact optimum (policy iteration)
+    sm = mdpgen.dense_dirichlet(2048, 16, alpha=0.1, gamma=0.999, seed=3, cost_dist="normal")
+    jstar, _, _ = exact.policy_iteration(sm)
+    dm = rmb.DeviceMDP.from_host(sm)
+    errs = {}
+    for name, form in (("f32", dm), ("bf16", rmb.dense_lowp(dm, rmb.RMB_P_BF16)),
+                       ("fp8", rmb.dense_lowp(dm, rmb.RMB_P_FP8E4M3))):
+        o = rmb.Opts(batch=256, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=400000, validate=False)
+        V2 = torch.zeros(2048, dtype=torch.float32, device="cuda")
+        st = rmb.rmb_vi(form, o, V2, stream=stream)
+        e = float(np.abs(V2.cpu().numpy() - jstar).max() / np.abs(jstar).max())
+        rec = {"sweeps": st["sweeps"], "ms": st["ms"], "rel_err_vs_exact": e}
+        if name != "f32":
+            V3 = torch.zeros(2048, dtype=torch.float32, device="cuda")
+            s1, s2 = rmb.rmb_vi_refined(form, dm, o, EPS, V3)
+            rec["refined_rel_err"] = float(np.abs(V3.cpu().numpy() - jstar).max() / np.abs(jstar).max())
+            rec["refined_sweeps"] = [s1["sweeps"], s2["sweeps"]]
+            rec["refined_ms"] = s1["ms"] + s2["ms"]
+        errs[name] = rec
+    best = max(thr, key=lambda r: r["p_stream_gbs"] if r["storage"] == "f32" else -1)
+    return _line("dense sweep throughput per P storage type (and converged error vs the exact optimum)",
+                 best["backups_per_s"], "Bellman backups/s", best["ms_per_sweep"], args, world,
+                 {"workload": "dense-mdp n=16384 m=16 dirichlet(0.1) c~N(0,1) gamma=0.999; 20 MB-VI sweeps "
+                              "per (storage, b); errors: same recipe at n=2048 solved to 1e-6",
+                  "p_gb_per_sweep_f32": n * m * n * 4 / 1e9},
+                 roofline={"bound": "hbm", "achieved": best["p_stream_gbs"], "peak": hbm, "unit": "GB/s",
+                           "frac": best["p_stream_gbs"] / hbm, "traffic": None,
+                           "kernel": "rmb_dense_kernel<f32>", "peak_kind": peak_kind},
+                 throughput=thr, full_solves=full, converged_errors_n2048=errs)
+
+
+def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
+    """256 uneven CSR MDPs: one graph-captured persistent launch vs one rmb_vi launch per MDP."""
+    mdps = mdpgen.config3()
+    dms = [rmb.DeviceMDP.from_host(x) for x in mdps]
+    tot_n = sum(x.n for x in mdps)
+    Vall = torch.zeros(tot_n, dtype=torch.float32, device="cuda")
+    Vs, off = [], 0
+    for x in mdps:
+        Vs.append(Vall[off:off + x.n])
+        off += x.n
+    o = rmb.Opts(batch=1, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=200000, validate=False)
+    s = torch.cuda.Stream()
+    B = rmb.Batch(dms, Vs, o, stream=s)
+    B.capture(s)
+
+    def step():
+        with torch.cuda.stream(s):
+            Vall.zero_()
+        B.replay(s)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    res = B.results(stream=s)
+    backups = sum(x.n * r["sweeps"] for x, r in zip(mdps, res))
+    nnz_passes = sum((r["sweeps"] + 1) * x.nnz * 8 for x, r in zip(mdps, res))
+    # the plain form: one rmb_vi launch per MDP, same b, one after the other
+    plan = B.plan_table()
+    seq_ms = 0.0
+    for x, dm, p in zip(mdps, dms, plan):
+        oo = rmb.Opts(batch=p["batch"], seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=200000, validate=False)
+        V = torch.zeros(x.n, dtype=torch.float32, device="cuda")
+        st = rmb.rmb_vi(dm, oo, V)
+        seq_ms += st["ms"]
+    return _line("batched time-to-1e-6 (all 256 MDPs) and Bellman backups/s", backups / (ms / 1e3),
+                 "Bellman backups/s", ms, args, world,
+                 {"workload": "256 csr-mdps n~logU[256,65536] m~U{2..16} k=16 dirichlet(1) c~U[0,1] "
+                              "gamma~U[0.9,0.99]; MB-VI to 1e-6, autotuned b, one graph-captured launch",
+                  "mdps": len(mdps), "total_states": tot_n, "total_nnz": sum(x.nnz for x in mdps),
+                  "time_to_eps_ms": ms, "plan_makespan_est_ms": B.handle.est_ms,
+                  "sequential_single_mdp_ms": seq_ms, "speedup_vs_sequential": seq_ms / ms,
+                  "groups": sorted({p["group_ctas"] for p in plan}),
+                  "max_sweeps": max(r["sweeps"] for r in res)},
+                 roofline={"bound": "hbm", "achieved": nnz_passes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                           "frac": nnz_passes / (ms / 1e3) / 1e9 / hbm, "traffic": None,
+                           "kernel": "rmb_batched_kernel", "peak_kind": peak_kind})
+
+
+def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
+    """n=65536, m=8, k=16 softmax MDP: forward MB-VI (gamma=0.95) and the adjoint gradient of w.V*."""
+    from oracle import exact
+    mdp = mdpgen.config5()
+    dm = rmb.DeviceMDP.from_host(mdp)
+    z = torch.from_numpy(mdp.logits).cuda()
+    w = torch.from_numpy(mdpgen.random_values(mdp.n, seed=13)).cuda()
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
+    fo = rmb.Opts(batch=4096, seed=mdpgen.PERM_SEED, eps=1e-7, max_sweeps=100000, validate=False)
+    go = rmb.Opts(batch=4096, seed=5, eps=1e-7, max_sweeps=100000)
+    fws = rmb.workspace(dm, fo)
+
+    def step():
+        rmb.rmb_softmax_rows(dm, z, dm.prob)
+        V.zero_()
+        st1 = rmb.rmb_vi(dm, fo, V, pi, None, ws=fws, stream=stream)
+        lam, gc, gz, st2 = rmb.rmb_fixed_point_grad(dm, pi, V, w, go)
+        return st1, st2
+
+    for _ in range(args.warmup):
+        step()
+    ms, outs = _timed(step, args.steps, stream)
+    st1, st2 = outs[-1]
+    t0 = time.perf_counter()
+    exact.fixed_point_gradient(mdp, w.cpu().numpy().astype(np.float64))
+    ct = time.perf_counter() - t0
+    return _line("time of forward solve + adjoint gradient (w.V*, dcost and dlogits)", 1e3 / ms, "gradients/s", ms,
+                 args, world,
+                 {"workload": "csr-mdp n=65536 m=8 k=16 P=softmax(N(0,1) logits) c~U[0,1] gamma=0.95; forward MB-VI "
+                              "b=4096 to 1e-7, adjoint mini-batch sweeps b=4096 to 1e-7",
+                  "forward_ms": st1["ms"], "forward_sweeps": st1["sweeps"], "adjoint_ms": st2["ms"],
+                  "adjoint_sweeps": st2["sweeps"]},
+                 roofline=None,
+                 cpu_baseline={"value": 1.0 / ct, "unit": "gradients/s", "cores": 0, "kind": "oracle",
+                               "sample": f"direct-solve gradient (policy iteration + GMRES adjoint), {ct:.1f} s"})
 
 
 if __name__ == "__main__":

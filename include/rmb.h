@@ -58,7 +58,8 @@ enum { RMB_DENSE = 0, RMB_CSR = 1 };
 
 /* Storage of dense transition rows.  RMB_P_F32 rows are used as given.  RMB_P_BF16 / RMB_P_FP8E4M3
    rows are codes c_rj = p_rj / scale_r (rmb_quantize_rows); the kernels decode them to float32 and
-   divide by the decoded row sum, so the scale cancels and every decoded row is a distribution. */
+   divide by the decoded row sum (taken from row_scale when given), so the quantisation scale cancels
+   and every decoded row is a distribution. */
 enum { RMB_P_F32 = 0, RMB_P_BF16 = 1, RMB_P_FP8E4M3 = 2 };
 
 /* The MDP (Sec. II-A).  All pointers are device pointers. */
@@ -75,7 +76,8 @@ typedef struct {
     int32_t k_uniform;       /* RMB_CSR: k > 0 declares row_ptr[r] == r*k for every row (enables
                                 the vectorised row path; checked when validate != 0); 0 = unknown */
     int32_t p_dtype;         /* RMB_DENSE: RMB_P_F32 / RMB_P_BF16 / RMB_P_FP8E4M3 */
-    const float *row_scale;  /* RMB_DENSE coded rows: [n*m] scales (informational; may be NULL) */
+    const float *row_scale;  /* RMB_DENSE coded rows: [n*m] = 1 / (sum of the row's decoded codes), as
+                                written by rmb_quantize_rows; NULL = the kernels sum each row */
 } rmb_mdp;
 
 /* Options of a solve. */
@@ -112,7 +114,7 @@ typedef struct {
     double v_shift;          /* centring offset mu at exit */
     int32_t status;          /* device-side rmb_status */
     int32_t grid_ctas;       /* CTAs of the persistent launch */
-    int32_t path;            /* 0 dense, 1 CSR vectorised rows, 2 CSR generic rows */
+    int32_t path;            /* 0 dense, 1 CSR vectorised rows, 2 CSR generic rows, 3 dense TMA pipeline */
     int32_t lanes_per_state; /* CSR paths: lanes that share one state */
     float ms;                /* device time of the call (CUDA events on `stream`) */
     int32_t reserved;
@@ -290,13 +292,14 @@ int rmb_batched_graph_launch(void *graph_exec, void *stream);
 int rmb_batched_graph_destroy(void *graph_exec);
 
 /*
- * Row quantiser: codes[r][j] = round-to-nearest-even(P[r][j] / scale[r]) in p_dtype, with
- * scale[r] = max_j P[r][j] / F (F = 1 for bf16, 448 = the largest finite e4m3 value for fp8, so
- * no code saturates; a zero row gets scale 1).  P [rows*cols] float32, codes [rows*cols] 2- or
- * 1-byte elements, scale [rows]: device.  The low-precision storage of the dense workload.
+ * Row quantiser: codes[r][j] = round-to-nearest-even(P[r][j] / s_r) in p_dtype, with
+ * s_r = max_j P[r][j] / F (F = 1 for bf16, 448 = the largest finite e4m3 value for fp8, so no code
+ * saturates; a zero row gets s_r = 1), and row_scale[r] = 1 / sum_j decode(codes[r][j]) (float32
+ * warp-order sum), the factor that turns decoded codes into the row's probabilities.
+ * P [rows*cols] float32, codes [rows*cols] 2- or 1-byte elements, row_scale [rows] or NULL: device.
  */
 int rmb_quantize_rows(const float *P, int64_t rows, int64_t cols, int32_t p_dtype, void *codes,
-                      float *scale, void *stream);
+                      float *row_scale, void *stream);
 
 /*
  * MB-VI with low-precision transition storage and float32 refinement: first MB-VI on `lowp`

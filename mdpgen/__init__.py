@@ -256,3 +256,28 @@ def config5(n: int = 65536, m: int = 8, k: int = 16, seed: int = 4) -> MDP:
     """CSR n=65536, m=8, k=16, P = softmax(N(0,1) logits), c ~ U[0,1], gamma=0.95."""
     return csr_uniform_k(n, m, k, gamma=0.95, seed=seed, prob_kind="softmax",
                          name=f"csr-softmax-k{k}-n{n}-m{m}")
+
+
+def dense_dirichlet_device(n: int, m: int, alpha: float, gamma: float, seed: int, cost_dist: str = "normal",
+                           device="cuda", block_rows: int = 2048, name: str = ""):
+    """Large dense Dirichlet(alpha) rows drawn directly in device memory with torch's seeded CUDA
+    generator (float64 Gamma draws, normalised, rounded to float32).  Same distribution as
+    `dense_dirichlet`, different random stream; for sizes whose host generation would take minutes.
+    Returns (P [n, m, n] float32 tensor, cost [n*m] float32 tensor)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    rows = n * m
+    P = torch.empty((rows, n), dtype=torch.float32, device=device)
+    conc = torch.full((block_rows, n), float(alpha), dtype=torch.float64, device=device)
+    for r0 in range(0, rows, block_rows):
+        r1 = min(rows, r0 + block_rows)
+        x = torch._standard_gamma(conc[: r1 - r0], generator=g)
+        s = x.sum(dim=1, keepdim=True)
+        x[:, 0] += (s[:, 0] <= 0).to(x.dtype)          # an all-underflow row becomes a point mass
+        P[r0:r1] = (x / x.sum(dim=1, keepdim=True)).to(torch.float32)
+    if cost_dist == "normal":
+        cost = torch.randn(rows, generator=g, dtype=torch.float64, device=device).to(torch.float32)
+    else:
+        cost = torch.rand(rows, generator=g, dtype=torch.float64, device=device).to(torch.float32)
+    return P.reshape(n, m, n), cost

@@ -39,7 +39,7 @@
 namespace rmb {
 
 enum Mode { MODE_VI = 0, MODE_EVAL = 1, MODE_MPI = 2, MODE_GREEDY = 3 };
-enum Path { PATH_DENSE = 0, PATH_CSR_VEC = 1, PATH_CSR_GEN = 2 };
+enum Path { PATH_DENSE = 0, PATH_CSR_VEC = 1, PATH_CSR_GEN = 2, PATH_DENSE_TMA = 3 };
 enum Kind { K_MIN = 0, K_POLICY = 1, K_GREEDY = 2 };
 
 constexpr int kCsrThreads = 512;
@@ -52,6 +52,7 @@ struct KP {
     // problem
     int n, m, k, path;
     int p_dtype;            // dense: RMB_P_F32 / RMB_P_BF16 / RMB_P_FP8E4M3
+    const float* row_scale; // dense coded rows: 1 / (sum of the row's decoded codes), or null
     const void* P;
     const int64_t* row_ptr;
     const int32_t* col;
@@ -571,7 +572,9 @@ __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole
 {
     constexpr int EB = Elem<DT>::bytes;
     constexpr int E = Elem<DT>::per16;
-    constexpr bool NORM = DT != RMB_P_F32;
+    // coded rows are normalised by the decoded row sum: read from row_scale when the quantiser
+    // stored it, accumulated here otherwise
+    const bool NORM = DT != RMB_P_F32 && p.row_scale == nullptr;
     const int n = p.n;
     const int nrows = pi_s >= 0 ? 1 : p.m;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -610,10 +613,22 @@ __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole
                             const uint4 w = __ldcs(reinterpret_cast<const uint4*>(rows[u] + (int64_t)c0 * EB) + jv);
                             float d[E];
                             decode16<DT>(w, d);
+                            // two partial chains per row (even / odd entries) keep the FMA chains short
+                            float x0 = 0.f, x1 = 0.f;
 #pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                acc[u] = fmaf(d[e], v[e], acc[u]);
-                                if (NORM) sum[u] += d[e];
+                            for (int e = 0; e < E; e += 2) {
+                                x0 = fmaf(d[e], v[e], x0);
+                                x1 = fmaf(d[e + 1], v[e + 1], x1);
+                            }
+                            acc[u] += x0 + x1;
+                            if (NORM) {
+                                float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+                                for (int e = 0; e < E; e += 2) {
+                                    y0 += d[e];
+                                    y1 += d[e + 1];
+                                }
+                                sum[u] += y0 + y1;
                             }
                         }
                     }
@@ -651,8 +666,9 @@ __device__ Best dense_state(const KP& p, DenseSmem& sm, float* stage, bool whole
                 tot += sm.red[w][tid];
                 tsum += sm.red2[w][tid];
             }
-            if (NORM) tot = tsum > 0.f ? tot / tsum : 0.f;
             const int a = pi_s >= 0 ? pi_s : a0 + tid;
+            if (NORM) tot = tsum > 0.f ? tot / tsum : 0.f;
+            else if (DT != RMB_P_F32) tot *= __ldg(p.row_scale + (int64_t)s * p.m + a);
             const float c = __ldg(p.cost + (int64_t)s * p.m + a);
             sm.q[a0 + tid] = (c == kInf) ? kInf : fmaf(p.gamma, tot, c);
         }
@@ -701,6 +717,234 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
         }
     }
     return true;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Dense path with a TMA pipeline: one producer warp streams the transition rows of the CTA's states,
+// row group by row group and column tile by column tile, into a ring of shared-memory stages with
+// cp.async.bulk (mbarrier transaction counts); eight consumer warps decode them and multiply with the
+// current values, staged once per batch.  Memory-level parallelism is the ring (kRingStages x
+// kStageBytes per SM), not registers, so coded rows (bf16 / fp8) stream as fast as float32 rows.
+// Every wait is bounded; after a timeout all threads still pass the same barriers (abort flag).
+// ------------------------------------------------------------------------------------------------
+constexpr int kTmaConsumers = 8;                    // consumer warps
+constexpr int kTmaThreads = (kTmaConsumers + 1) * 32;
+constexpr int kRingStages = 4;
+constexpr int kStageBytes = 32768;
+constexpr int kTmaRowGroup = 8;                     // rows per stage (all-action passes)
+constexpr int kTmaMaxStates = 512;                  // states per chunk of a batch
+
+struct TmaSmem {
+    uint64_t full[kRingStages];
+    uint64_t empty[kRingStages];
+    uint64_t vbar;
+    uint32_t vphase;
+    int abort;
+    int ids[kTmaMaxStates];
+    int pis[kTmaMaxStates];
+    float red[kTmaConsumers][kTmaRowGroup];
+    float q[kDenseMaxM];
+};
+
+__device__ __forceinline__ bool mb_try(uint32_t mb, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{ .reg .pred q; mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2; selp.u32 %0, 1, 0, q; }"
+                 : "=r"(done) : "r"(mb), "r"(parity) : "memory");
+    return done != 0;
+}
+
+// bounded wait; returns false (and raises the abort flag and the error) on timeout or abort
+__device__ __forceinline__ bool mb_wait(uint32_t mb, uint32_t parity, const KP& p, volatile int* abort_flag)
+{
+    if (*abort_flag) return false;
+    const uint64_t t0 = globaltimer_ns();
+    uint32_t spins = 0;
+    while (!mb_try(mb, parity)) {
+        if ((++spins & 63u) == 0) {
+            if (*abort_flag) return false;
+            if ((int64_t)(globaltimer_ns() - t0) > p.timeout_ns) {
+                *abort_flag = 1;
+                atomicCAS(&p.ctrl->error, 0, RMB_ERR_BARRIER_TIMEOUT);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTmaConsumers * 32) : "memory"); }
+
+template <int KIND, int DT>
+__device__ bool dense_batch_tma(const KP& p, const GroupView& gv, TmaSmem& sm, float* vst, unsigned char* ring,
+                                uint32_t& ring_it, const float* A, float* B, int pos0, int len, const PermKey* K,
+                                int32_t* Sout, float* Wout, const Centre& C, Acc& acc, bool* perm_ok)
+{
+    constexpr int EB = Elem<DT>::bytes;
+    constexpr int E = Elem<DT>::per16;
+    const int n = p.n;
+    const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+    const bool producer = wid == kTmaConsumers;
+    const int RG = KIND == K_POLICY ? 1 : kTmaRowGroup;
+    const int nrows = KIND == K_POLICY ? 1 : p.m;
+    const int TC = min(n, (kStageBytes / (RG * EB)) & ~15);       // columns per tile
+    const int ntiles = (n + TC - 1) / TC;
+    const int ngroups = (nrows + RG - 1) / RG;
+    const int G = gv.size, me = gv.rank;
+    if (me >= len) return true;
+    volatile int* abort_flag = &sm.abort;
+    // stage the current values once per batch (bulk copy into this CTA's shared memory)
+    const uint32_t vb = (uint32_t)__cvta_generic_to_shared(&sm.vbar);
+    if (tid == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        const uint32_t bytes = (uint32_t)((n + 3) & ~3) * 4u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(vb), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(vst)), "l"(A), "r"(bytes), "r"(vb) : "memory");
+    }
+    const bool v_ok = mb_wait(vb, sm.vphase & 1u, p, abort_flag);
+    __syncthreads();
+    if (tid == 0) sm.vphase++;
+    if (!v_ok || *abort_flag) return false;
+    const unsigned char* P = static_cast<const unsigned char*>(p.P);
+    const int total = (len - me + G - 1) / G;                     // this CTA's states in the batch
+    for (int c0 = 0; c0 < total; c0 += kTmaMaxStates) {
+        const int cnt = min(kTmaMaxStates, total - c0);
+        __syncthreads();
+        for (int i = tid; i < cnt; i += blockDim.x) {
+            const int pos = me + (c0 + i) * G;
+            const int st = K ? state_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
+            sm.ids[i] = st;
+            sm.pis[i] = KIND == K_POLICY
+                            ? (int)min((uint32_t)ld_l2(p.pi_in ? p.pi_in + st : p.pi + st), (uint32_t)(p.m - 1))
+                            : 0;
+        }
+        __syncthreads();
+        if (producer) {
+            if (lane == 0) {
+                uint32_t it = ring_it;
+                for (int i = 0; i < cnt; ++i) {
+                    const int s = sm.ids[i];
+                    for (int g = 0; g < ngroups; ++g) {
+                        const int a0 = g * RG;
+                        const int rg = min(RG, nrows - a0);
+                        for (int t = 0; t < ntiles; ++t, ++it) {
+                            const int slot = it % kRingStages;
+                            const uint32_t use = it / kRingStages;
+                            const uint32_t fb = (uint32_t)__cvta_generic_to_shared(&sm.full[slot]);
+                            if (use > 0 && !mb_wait((uint32_t)__cvta_generic_to_shared(&sm.empty[slot]), (use - 1) & 1u, p,
+                                                    abort_flag))
+                                continue;
+                            const int width = min(TC, n - t * TC);
+                            const uint32_t bytes = (uint32_t)(rg * width * EB);
+                            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes)
+                                         : "memory");
+                            unsigned char* dst = ring + (size_t)slot * kStageBytes;
+                            for (int r = 0; r < rg; ++r) {
+                                const int a = KIND == K_POLICY ? sm.pis[i] : a0 + r;
+                                const unsigned char* src = P + (((int64_t)s * p.m + a) * n + (int64_t)t * TC) * EB;
+                                asm volatile(
+                                    "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                    ::"r"((uint32_t)__cvta_generic_to_shared(dst + (size_t)r * width * EB)), "l"(src),
+                                    "r"((uint32_t)(width * EB)), "r"(fb) : "memory");
+                            }
+                        }
+                    }
+                }
+                // on abort, let the copies already issued land before the CTA moves on
+                if (*abort_flag) {
+                    const uint32_t first = it > (uint32_t)kRingStages ? it - kRingStages : 0u;
+                    for (uint32_t k = first; k < it; ++k) {
+                        const uint32_t fb = (uint32_t)__cvta_generic_to_shared(&sm.full[k % kRingStages]);
+                        const uint64_t t0 = globaltimer_ns();
+                        while (!mb_try(fb, (k / kRingStages) & 1u) &&
+                               (int64_t)(globaltimer_ns() - t0) < p.timeout_ns) {
+                        }
+                    }
+                }
+            }
+        } else {
+            uint32_t it = ring_it;
+            for (int i = 0; i < cnt; ++i) {
+                const int s = sm.ids[i];
+                for (int g = 0; g < ngroups; ++g) {
+                    const int a0 = g * RG;
+                    const int rg = min(RG, nrows - a0);
+                    float accv[kTmaRowGroup];
+#pragma unroll
+                    for (int r = 0; r < kTmaRowGroup; ++r) accv[r] = 0.f;
+                    for (int t = 0; t < ntiles; ++t, ++it) {
+                        const int slot = it % kRingStages;
+                        const bool ok = mb_wait((uint32_t)__cvta_generic_to_shared(&sm.full[slot]),
+                                                (it / kRingStages) & 1u, p, abort_flag);
+                        if (ok) {
+                            const int width = min(TC, n - t * TC);
+                            const unsigned char* st = ring + (size_t)slot * kStageBytes;
+                            const float* vt = vst + (size_t)t * TC;
+                            for (int jv = tid; jv < width / E; jv += kTmaConsumers * 32) {
+                                float v[E];
+#pragma unroll
+                                for (int q = 0; q < E / 4; ++q) {
+                                    const float4 f = reinterpret_cast<const float4*>(vt)[jv * (E / 4) + q];
+                                    v[4 * q] = f.x;
+                                    v[4 * q + 1] = f.y;
+                                    v[4 * q + 2] = f.z;
+                                    v[4 * q + 3] = f.w;
+                                }
+#pragma unroll
+                                for (int r = 0; r < kTmaRowGroup; ++r) {
+                                    if (r < rg) {
+                                        const uint4 w = reinterpret_cast<const uint4*>(st + (size_t)r * width * EB)[jv];
+                                        float d[E];
+                                        decode16<DT>(w, d);
+                                        float x0 = 0.f, x1 = 0.f;
+#pragma unroll
+                                        for (int e = 0; e < E; e += 2) {
+                                            x0 = fmaf(d[e], v[e], x0);
+                                            x1 = fmaf(d[e + 1], v[e + 1], x1);
+                                        }
+                                        accv[r] += x0 + x1;
+                                    }
+                                }
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0 && ok)
+                            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];"
+                                         ::"r"((uint32_t)__cvta_generic_to_shared(&sm.empty[slot])) : "memory");
+                    }
+                    // row sums over the consumer warps
+#pragma unroll
+                    for (int r = 0; r < kTmaRowGroup; ++r) {
+                        float x = accv[r];
+                        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+                        if (lane == 0) sm.red[wid][r] = x;
+                    }
+                    consumer_sync();
+                    if (tid < rg) {
+                        float tot = 0.f;
+                        for (int w = 0; w < kTmaConsumers; ++w) tot += sm.red[w][tid];
+                        const int a = KIND == K_POLICY ? sm.pis[i] : a0 + tid;
+                        const int64_t r = (int64_t)s * p.m + a;
+                        if (DT != RMB_P_F32) tot *= __ldg(p.row_scale + r);
+                        const float c = __ldg(p.cost + r);
+                        sm.q[KIND == K_POLICY ? 0 : a0 + tid] = (c == kInf) ? kInf : fmaf(p.gamma, tot, c);
+                    }
+                    consumer_sync();
+                }
+                if (tid == 0 && !*abort_flag) {
+                    Best best = {kInf, 0x7fffffff, kInf};
+                    for (int ai = 0; ai < nrows; ++ai)
+                        best = better(best, Best{sm.q[ai], KIND == K_POLICY ? sm.pis[i] : ai, kInf});
+                    state_epilogue<KIND>(p, best, s, me + (c0 + i) * G, A, B, Sout, Wout, C, acc);
+                }
+            }
+        }
+        // every thread advances the ring counter by the tiles of this chunk
+        ring_it += (uint32_t)(cnt * ngroups * ntiles);
+    }
+    __syncthreads();
+    return *abort_flag == 0;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -769,6 +1013,9 @@ struct Runner {
     bool perm_ok;
     GroupView gv;
     bool lead;   // thread 0 of the group's first CTA
+    TmaSmem* tsm = nullptr;        // dense TMA path: barriers, state lists
+    unsigned char* ring = nullptr; // dense TMA path: stage ring
+    uint32_t ring_it = 0;          // dense TMA path: tiles streamed so far (same in every thread)
 
     __device__ Runner(const KP& kp, RedSmem& r, DenseSmem* d, float* st, GroupView g)
         : p(kp), c(kp.ctrl), target(0), barriers(0), stall(false), cur(0), red_epoch(0), rs(r), dsm(d),
@@ -807,6 +1054,11 @@ struct Runner {
     __device__ bool batch(const float* A, float* B, int pos0, int len, const PermKey* K, int32_t* So, float* Wo,
                           Acc& acc)
     {
+        if (PATH == PATH_DENSE_TMA) {
+            constexpr int DT = NCA;
+            return dense_batch_tma<KIND, DT>(p, gv, *tsm, stage, ring, ring_it, A, B, pos0, len, K, So, Wo, C, acc,
+                                             &perm_ok);
+        }
         if (PATH == PATH_DENSE) {
             // dense kernels are instantiated per storage type: NCA carries the element type
             constexpr int DT = NCA;
@@ -979,6 +1231,17 @@ struct Runner {
     __device__ void run()
     {
         stall = (p.flags & RMB_FLAG_INJECT_BARRIER_STALL) && gv.rank == 0;
+        if (PATH == PATH_DENSE_TMA && threadIdx.x == 0) {
+            for (int i = 0; i < kRingStages; ++i) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->full[i])) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->empty[i])),
+                             "r"(kTmaConsumers) : "memory");
+            }
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->vbar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            tsm->vphase = 0;
+            tsm->abort = 0;
+        }
         if (PATH == PATH_DENSE && threadIdx.x == 0) {
             const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&dsm->mbar);
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
@@ -1093,6 +1356,21 @@ __global__ void __launch_bounds__(kCsrThreads, 2) rmb_csr_gen_kernel(KP p)
 {
     __shared__ RedSmem rs;
     Runner<PATH_CSR_GEN> R(p, rs, nullptr, nullptr, GroupView{(int)blockIdx.x, (int)gridDim.x});
+    R.run();
+}
+
+// Dense rows streamed by the TMA pipeline; DT = element type of P.  Dynamic shared memory: the
+// staged values (vst_floats) followed by the stage ring.
+template <int DT>
+__global__ void __launch_bounds__(kTmaThreads, 1) rmb_dense_tma_kernel(KP p)
+{
+    __shared__ RedSmem rs;
+    __shared__ __align__(16) TmaSmem tsm;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    float* vst = reinterpret_cast<float*>(dyn);
+    Runner<PATH_DENSE_TMA, DT> R(p, rs, nullptr, vst, GroupView{(int)blockIdx.x, (int)gridDim.x});
+    R.tsm = &tsm;
+    R.ring = dyn + (size_t)p.stage * 4;
     R.run();
 }
 
@@ -1285,14 +1563,25 @@ __global__ void rmb_quantize_kernel(const float* __restrict__ P, int64_t rows, i
         for (int64_t j = lane; j < cols; j += 32) mx = fmaxf(mx, row[j]);
         for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
         const float sc = mx > 0.f ? (dt == RMB_P_FP8E4M3 ? mx / 448.f : mx) : 1.f;
-        if (lane == 0 && scale) scale[r] = sc;
+        float dsum = 0.f;   // sum of the decoded codes
         if (dt == RMB_P_BF16) {
             __nv_bfloat16* out = static_cast<__nv_bfloat16*>(codes) + r * cols;
-            for (int64_t j = lane; j < cols; j += 32) out[j] = __float2bfloat16_rn(row[j] / sc);
+            for (int64_t j = lane; j < cols; j += 32) {
+                const __nv_bfloat16 c = __float2bfloat16_rn(row[j] / sc);
+                out[j] = c;
+                dsum += __bfloat162float(c);
+            }
         } else {
             __nv_fp8_storage_t* out = static_cast<__nv_fp8_storage_t*>(codes) + r * cols;
-            for (int64_t j = lane; j < cols; j += 32) out[j] = __nv_cvt_float_to_fp8(row[j] / sc, __NV_SATFINITE, __NV_E4M3);
+            for (int64_t j = lane; j < cols; j += 32) {
+                const __nv_fp8_storage_t c = __nv_cvt_float_to_fp8(row[j] / sc, __NV_SATFINITE, __NV_E4M3);
+                out[j] = c;
+                const __half_raw h = __nv_cvt_fp8_to_halfraw(c, __NV_E4M3);
+                dsum += __half2float(*reinterpret_cast<const __half*>(&h));
+            }
         }
+        for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, off);
+        if (lane == 0 && scale) scale[r] = dsum > 0.f ? 1.f / dsum : 0.f;
     }
 }
 
@@ -1549,6 +1838,7 @@ int fill_kp(int mode, const rmb_mdp* M, const rmb_opts* O, int64_t b, char* ws, 
     p.k = M->format == RMB_CSR ? M->k_uniform : 0;
     p.P = M->P;
     p.p_dtype = M->format == RMB_DENSE ? M->p_dtype : RMB_P_F32;
+    p.row_scale = (M->format == RMB_DENSE && M->p_dtype != RMB_P_F32) ? M->row_scale : nullptr;
     p.row_ptr = M->row_ptr;
     p.col = M->col;
     p.prob = M->prob;
@@ -1635,7 +1925,7 @@ int solve(const Call& q)
 
     char* ws = static_cast<char*>(q.ws);
     KP p;
-    const int path = fill_kp(q.mode, M, O, b, ws, L, reinterpret_cast<Ctrl*>(ws + L.ctrl), p);
+    int path = fill_kp(q.mode, M, O, b, ws, L, reinterpret_cast<Ctrl*>(ws + L.ctrl), p);
     p.Vin = q.Vin;
     p.Vout = q.Vout;
     p.TVout = q.TV;
@@ -1646,6 +1936,30 @@ int solve(const Call& q)
     const void* fn;
     int threads, per_sm;
     size_t smem = 0;
+    if (path == PATH_DENSE) {
+        // large rows stream through the TMA pipeline when the staged values and the ring fit
+        const int e16 = p.p_dtype == RMB_P_F32 ? 4 : (p.p_dtype == RMB_P_BF16 ? 8 : 16);
+        const size_t vbytes = align_up((size_t)((M->n + 3) & ~3LL) * 4, 128);
+        const size_t tma_smem = vbytes + (size_t)kRingStages * kStageBytes;
+        const bool tma_ok = M->n >= 2048 && M->n % e16 == 0 && (((uintptr_t)M->P) & 15) == 0 &&
+                            (p.p_dtype == RMB_P_F32 || p.row_scale) && tma_smem + sizeof(TmaSmem) + 2048 <= 227 * 1024 &&
+                            !std::getenv("RMB_DENSE_NO_TMA");
+        if (tma_ok) {
+            path = PATH_DENSE_TMA;
+            p.path = path;
+            fn = p.p_dtype == RMB_P_BF16      ? reinterpret_cast<const void*>(rmb_dense_tma_kernel<RMB_P_BF16>)
+                 : p.p_dtype == RMB_P_FP8E4M3 ? reinterpret_cast<const void*>(rmb_dense_tma_kernel<RMB_P_FP8E4M3>)
+                                              : reinterpret_cast<const void*>(rmb_dense_tma_kernel<RMB_P_F32>);
+            threads = kTmaThreads;
+            p.stage = (int)(vbytes / 4);
+            smem = tma_smem;
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return RMB_ERR_CUDA;
+            int occ = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess) return RMB_ERR_CUDA;
+            per_sm = occ < 2 ? occ : 2;
+        }
+    }
     if (path == PATH_DENSE) {
         fn = p.p_dtype == RMB_P_BF16      ? reinterpret_cast<const void*>(rmb_dense_kernel<RMB_P_BF16>)
              : p.p_dtype == RMB_P_FP8E4M3 ? reinterpret_cast<const void*>(rmb_dense_kernel<RMB_P_FP8E4M3>)
@@ -1664,7 +1978,7 @@ int solve(const Call& q)
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess)
             return RMB_ERR_CUDA;
         per_sm = occ < 2 ? occ : 2;
-    } else {
+    } else if (path != PATH_DENSE_TMA) {
         fn = path == PATH_CSR_VEC ? csr_vec_kernel_for(p.nc_all, p.nc_one)
                                   : reinterpret_cast<const void*>(rmb_csr_gen_kernel);
         threads = kCsrThreads;

@@ -66,7 +66,8 @@ def test_quantiser_matches_cpu_conversion(dt):
     dm = rmb.DeviceMDP.from_host(mdp)
     codes, scale = rmb.rmb_quantize_rows(dm.P.reshape(-1), P2.shape[0], P2.shape[1], dt)
     want, sc = cpu_codes(P2, dt)
-    assert torch.equal(scale.cpu(), sc)
+    dec_sum = want.to(torch.float64).sum(dim=1)
+    assert torch.allclose(1.0 / scale.cpu().to(torch.float64), dec_sum, rtol=1e-6, atol=0)
     if dt == rmb.RMB_P_FP8E4M3:
         assert torch.equal(codes.cpu().reshape(P2.shape), want.view(torch.uint8))
     else:
@@ -87,6 +88,20 @@ def test_lowp_trajectory_matches_oracle_on_decoded_rows(dt, n, m, b):
     st = rmb.rmb_vi(lp, rmb.Opts(batch=b, seed=9, eps=0.0, max_sweeps=4), V)
     assert st["sweeps"] == 4 and st["path"] == "dense"
     close(V.cpu().numpy(), ref["traj"][3])
+
+
+@pytest.mark.parametrize("dt", [rmb.RMB_P_BF16, rmb.RMB_P_FP8E4M3])
+def test_row_sums_from_quantiser_or_on_the_fly_agree(dt):
+    mdp = mdpgen.dense_dirichlet(640, 8, alpha=0.1, gamma=0.99, seed=2, cost_dist="normal")
+    dm = rmb.DeviceMDP.from_host(mdp)
+    lp = rmb.dense_lowp(dm, dt)
+    raw = rmb.DeviceMDP(lp.n, lp.m, lp.gamma, "dense", lp.cost, P=lp.P, p_dtype=dt, row_scale=None)
+    out = []
+    for form in (lp, raw):
+        V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+        rmb.rmb_vi(form, rmb.Opts(batch=32, seed=4, eps=0.0, max_sweeps=30), V)
+        out.append(V.cpu().numpy())
+    close(out[0], out[1].astype(np.float64), tol=1e-6)
 
 
 @pytest.mark.parametrize("dt", [rmb.RMB_P_BF16, rmb.RMB_P_FP8E4M3])
