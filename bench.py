@@ -303,6 +303,24 @@ def main():
                 "bytes_per_launch": statistics.mean(per_launch_bytes),
                 "note": "P stream (prob+col+cost) per sweep x (sweeps + 1 greedy pass) / launch time"}
 
+    # the measured ceiling of the real bound: random 4-byte gathers from a table the size of the values
+    g_idx = torch.randint(0, n, (1 << 27,), dtype=torch.int32, device=dev,
+                          generator=torch.Generator(device=dev).manual_seed(7))
+    g_src = torch.rand(n, dtype=torch.float32, device=dev)
+    rmb.rmb_gather_probe(g_src, g_idx, reps=1, stream=stream)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    rmb.rmb_gather_probe(g_src, g_idx, reps=4, stream=stream)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    ceiling = 4 * g_idx.numel() / (pe0.elapsed_time(pe1) / 1e3)
+    del g_idx, g_src
+    gathers = sum((st["sweeps"] + 1) * n * M_ACTIONS * K_SUCC for st in stats)
+    roofline["gather_bound"] = {"rate_per_s": gathers / (kernel_ms / 1e3), "ceiling_per_s": ceiling,
+                                "frac": gathers / (kernel_ms / 1e3) / ceiling,
+                                "note": "random successor gathers (one 32-byte L2 sector each) vs the measured rate "
+                                        "of random 4-byte gathers from a 4 MB table (rmb_gather_probe)"}
+
     # end to end through the public API: pinned host inputs copied in, V and pi copied out, every step
     e2e = None
     if rank == 0 or world > 1:

@@ -312,6 +312,16 @@ int rmb_vi_refined(const rmb_mdp *lowp, const rmb_mdp *ref, const rmb_opts *opts
                    float *V_inout, int32_t *pi_out, float *qgap_out, void *workspace,
                    size_t workspace_bytes, rmb_stats *stats_low, rmb_stats *stats_ref, void *stream);
 
+/*
+ * Diagnostic (not part of the method): the attainable rate of random 4-byte gathers.  One CTA of 512
+ * threads per SM streams idx (int32, 16-byte aligned, n_idx a multiple of 4) and gathers src[idx]
+ * through L1, reps times; out receives one checksum per thread (grid_size * 512 floats, grid_size =
+ * number of SMs).  With src sized like the value vector and uniformly random idx this measures the
+ * L1->L2 request ceiling that bounds the CSR sweeps.
+ */
+int rmb_gather_probe(const float *src, int64_t n_src, const int32_t *idx, int64_t n_idx, int reps,
+                     float *out, void *stream);
+
 /* Static text for a status code. */
 const char *rmb_status_string(int status);
 

@@ -419,6 +419,23 @@ def rmb_vi_refined(lowp: DeviceMDP, ref: DeviceMDP, opts: Opts, eps_low: float, 
     return s1.as_dict(), s2.as_dict()
 
 
+def rmb_gather_probe(src, idx, reps: int = 1, stream=None):
+    """Diagnostic: gather src[idx] (reps times) with one 512-thread CTA per SM; returns the checksums."""
+    import torch
+    _check(src, torch.float32, 1, "src")
+    _check(idx, torch.int32, 4, "idx")
+    out = torch.empty(torch.cuda.get_device_properties(src.device).multi_processor_count * 512,
+                      dtype=torch.float32, device=src.device)
+    f = lib().rmb_gather_probe
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    st = f(_ptr(src), src.numel(), _ptr(idx), idx.numel(), int(reps), _ptr(out), _stream_handle(stream))
+    if st != RMB_OK:
+        raise RmbError(st, "rmb_gather_probe")
+    return out
+
+
 def rmb_permutation(n: int, seed: int, sweep: int, out=None, stream=None):
     """sigma_{seed,sweep}(p) for p = 0..n-1 as an int32 CUDA tensor."""
     import torch

@@ -1092,9 +1092,9 @@ struct Runner {
         if (KIND == K_MIN && NCA > 0) fast_prefetch_first<K_MIN, NCA_>(p, gv, p.lps_all, pos0, len, K, carry_a, &perm_ok);
     }
 
-    __device__ void copy_batch(const int32_t* S, const float* Wv, int len, float* B)
+    __device__ void copy_batch(const int32_t* S, const float* Wv, int len, float* B, size_t skip = 0)
     {
-        for (size_t i = gtid(); i < (size_t)len; i += gthreads()) st_l2(B + ld_l2(S + i), ld_l2(Wv + i));
+        for (size_t i = gtid() + skip; i < (size_t)len; i += gthreads()) st_l2(B + ld_l2(S + i), ld_l2(Wv + i));
     }
 
     // Re-centre between sweeps when the midpoint of the values moved by more than a quarter of
@@ -1154,9 +1154,18 @@ struct Runner {
             float* A = p.d[(cur + t) & 1];
             float* B = p.d[(cur + t + 1) & 1];
             const int len = (t == p.T - 1) ? p.last_len : p.b;
+            // B must also receive batch t-1's new values before the next batch reads it: the first
+            // item of each thread is loaded before the batch's compute and stored after it
+            int c_s = -1;
+            float c_v = 0.f;
+            const size_t c0 = gtid();
+            if (t >= 1 && c0 < (size_t)p.b) {
+                c_s = ld_l2(p.S[(t - 1) & 1] + c0);
+                c_v = ld_l2(p.W[(t - 1) & 1] + c0);
+            }
             if (!batch<KIND>(A, B, t * p.b, len, &K, p.S[t & 1], p.W[t & 1], acc)) return false;
-            // B must also receive batch t-1's new values before the next batch reads it
-            if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B);
+            if (c_s >= 0) st_l2(B + c_s, c_v);
+            if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B, gthreads());
             if (t == p.T - 1) publish(c, slot, acc, rs);
             arrive();
             if (t + 1 < p.T) prefetch_next<KIND>((t + 1) * p.b, (t + 2 == p.T) ? p.last_len : p.b, &K);
@@ -1548,6 +1557,26 @@ __global__ void rmb_grad_kernel(int n, int m, int k, float gamma, const int32_t*
             grad_z[r * k + t] = gamma * l * pv * (vj - mean);
         }
     }
+}
+
+// Gather-rate probe: every thread streams 16-byte chunks of an index array and gathers src at those
+// indices (L1-cached, as the successor gathers), accumulating a checksum per thread.  Measures the
+// attainable rate of random 4-byte gathers from a table of a given size (the CSR kernel's L2 bound).
+__global__ void __launch_bounds__(512, 1) rmb_gather_probe_kernel(const float* __restrict__ src, uint32_t nm1,
+                                                                  const int4* __restrict__ idx, int64_t n4, int reps,
+                                                                  float* __restrict__ out)
+{
+    float acc = 0.f;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r) {
+        for (int64_t i = t; i < n4; i += T) {
+            const int4 c = __ldcs(idx + i);
+            acc += __ldca(src + min((uint32_t)c.x, nm1)) + __ldca(src + min((uint32_t)c.y, nm1)) +
+                   __ldca(src + min((uint32_t)c.z, nm1)) + __ldca(src + min((uint32_t)c.w, nm1));
+        }
+    }
+    out[t] = acc;
 }
 
 // Row quantiser (low-precision storage of dense rows): one warp per row.
@@ -2639,6 +2668,22 @@ int rmb_vi_refined(const rmb_mdp* lowp, const rmb_mdp* ref, const rmb_opts* opts
     Call q2{MODE_VI, ref, &o2, V_inout, V_inout, nullptr, pi_out, qgap_out, nullptr,
             workspace, workspace_bytes, stats_ref, static_cast<cudaStream_t>(stream)};
     return solve(q2);
+}
+
+int rmb_gather_probe(const float* src, int64_t n_src, const int32_t* idx, int64_t n_idx, int reps, float* out,
+                     void* stream)
+{
+    if (!src || !idx || !out || n_src < 1 || n_src >= ((int64_t)1 << 32) || n_idx < 4 || (n_idx & 3) || reps < 1)
+        return RMB_ERR_ARG;
+    if (((uintptr_t)idx) & 15) return RMB_ERR_ARG;
+    DevInfo* D = nullptr;
+    int st = dev_info(&D);
+    if (st) return st;
+    cudaFuncSetAttribute(rmb_gather_probe_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    rmb_gather_probe_kernel<<<D->sms, 512, 0, static_cast<cudaStream_t>(stream)>>>(
+        src, (uint32_t)(n_src - 1), reinterpret_cast<const int4*>(idx), n_idx / 4, reps, out);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
 }
 
 const char* rmb_status_string(int status)
