@@ -104,6 +104,13 @@ typedef struct {
 /* Rows need not sum to 1 (used for the transposed chain of rmb_fixed_point_grad): values are kept
    uncentred (mu = 0) and the sweeps run in plain float32. */
 #define RMB_FLAG_RAW_ROWS 2
+/* Asynchronous sweeps (RMB_CSR only, single-MDP solves: rmb_vi, rmb_mpi, rmb_eval_policy,
+   rmb_vi_noalloc; others return RMB_ERR_UNSUPPORTED. Sec. V suggests asynchronous MB-VI / MB-MPI): a
+   sweep processes the whole random order of its permutation in one pass and writes every new value in
+   place at once, with no grid-wide barrier between batches, so a state reads whatever updates of the
+   same sweep have already landed (chaotic relaxation; b is ignored).  One barrier per sweep keeps
+   the stop test.  Converges to the same fixed point; trajectories are not reproducible. */
+#define RMB_FLAG_ASYNC 4
 
 /* Results of a solve (filled only when a stats pointer is passed). */
 typedef struct {

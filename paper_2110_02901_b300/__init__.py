@@ -38,6 +38,7 @@ RMB_P_BF16 = 1
 RMB_P_FP8E4M3 = 2
 RMB_FLAG_INJECT_BARRIER_STALL = 1
 RMB_FLAG_RAW_ROWS = 2
+RMB_FLAG_ASYNC = 4
 PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic", 3: "dense-tma"}
 
 

@@ -68,7 +68,7 @@ struct KP {
     int lps_all, lps_one;   // CSR: lanes sharing one state (all actions / one row)
     int nc_all, nc_one;     // CSR vectorised: float4 chunks per lane per state (0 = general loop)
     int k4_log2;            // CSR vectorised: log2(k/4)
-    int32_t* perm_buf;      // non-null when a sweep has >= 4 batches: sigma of the coming sweep
+    int32_t* perm_buf;      // non-null when a sweep has >= 16 batches: sigma of the coming sweep
     int stage;              // dense: floats of V staged per chunk
     // buffers
     const float* Vin;
@@ -241,8 +241,10 @@ __device__ __forceinline__ void state_epilogue(const KP& p, const Best& r, int s
         acc.dmax = fmaxf(acc.dmax, fabsf(v - old));
         acc.vlo = fminf(acc.vlo, v);
         acc.vhi = fmaxf(acc.vhi, v);
-        st_l2(Sout + i, s);
-        st_l2(Wout + i, v);
+        if (Sout) {
+            st_l2(Sout + i, s);
+            st_l2(Wout + i, v);
+        }
         st_l2(B + s, v);
     }
 }
@@ -451,8 +453,10 @@ __device__ void csr_batch_fast(const KP& p, const GroupView& gv, int lps, const 
                 acc.vlo = fminf(acc.vlo, v);
                 acc.vhi = fmaxf(acc.vhi, v);
                 const int i = G.first + G.g + j * G.U;
-                st_l2(Sout + i, s_cur);
-                st_l2(Wout + i, v);
+                if (Sout) {
+                    st_l2(Sout + i, s_cur);
+                    st_l2(Wout + i, v);
+                }
                 st_l2(B + s_cur, v);
             }
         }
@@ -1150,7 +1154,17 @@ struct Runner {
         }
         ++red_epoch;
         Acc acc = {0.f, kInf, -kInf};
-        for (int t = 0; t < p.T; ++t) {
+        const bool async = (p.flags & RMB_FLAG_ASYNC) != 0;
+        if (async) {
+            // asynchronous sweep: the whole order in one pass, every new value written in place at once
+            // (no barrier between batches: later states read whatever updates have landed)
+            float* A = p.d[cur];
+            K.buf = nullptr;
+            if (!batch<KIND>(A, A, 0, p.n, &K, nullptr, nullptr, acc)) return false;
+            publish(c, slot, acc, rs);
+            if (!sync(12)) return false;
+        }
+        for (int t = 0; t < (async ? 0 : p.T); ++t) {
             float* A = p.d[(cur + t) & 1];
             float* B = p.d[(cur + t + 1) & 1];
             const int len = (t == p.T - 1) ? p.last_len : p.b;
@@ -1173,7 +1187,7 @@ struct Runner {
         }
         float lo, hi;
         read_slot(c, slot, rs, delta, lo, hi);
-        const int newcur = (cur + p.T) & 1;
+        const int newcur = async ? cur : (cur + p.T) & 1;
         if (lead && p.trace && j >= 0) p.trace[j] = (double)delta;
         stop = can_stop && ((double)delta <= p.eps || is_last);
         if (delta != delta) {
@@ -1189,12 +1203,12 @@ struct Runner {
             for (size_t i = gtid(); i < (size_t)p.n; i += gthreads()) {
                 const float v = ld_l2(F + i) - shift;
                 st_l2(F + i, v);
-                st_l2(O + i, v);
+                if (!async) st_l2(O + i, v);
             }
             C = make_centre(C.mu + (double)shift, p.gamma_d);
             compute_perm(k + 1);
             if (!sync(20)) return false;
-        } else if (p.T >= 2) {
+        } else if (p.T >= 2 && !async) {
             copy_batch(p.S[(p.T - 1) & 1], p.W[(p.T - 1) & 1], p.last_len, p.d[cur ^ 1]);
             compute_perm(k + 1);
             if (!sync(21)) return false;
@@ -1891,7 +1905,9 @@ int fill_kp(int mode, const rmb_mdp* M, const rmb_opts* O, int64_t b, char* ws, 
     p.S[1] = reinterpret_cast<int32_t*>(ws + L.s1);
     p.W[0] = reinterpret_cast<float*>(ws + L.w0);
     p.W[1] = reinterpret_cast<float*>(ws + L.w1);
-    p.perm_buf = (L.perm_buf && mode != MODE_GREEDY) ? reinterpret_cast<int32_t*>(ws + L.pb) : nullptr;
+    // asynchronous sweeps have no barrier before a sweep's first read, so sigma is computed on the fly
+    const bool async = (O->flags & RMB_FLAG_ASYNC) != 0;
+    p.perm_buf = (L.perm_buf && mode != MODE_GREEDY && !async) ? reinterpret_cast<int32_t*>(ws + L.pb) : nullptr;
     p.ctrl = ctrl;
     p.trace = mode == MODE_GREEDY ? nullptr : O->trace;
     p.timeout_ns = O->barrier_timeout_ns > 0 ? O->barrier_timeout_ns : 2000000000LL;
@@ -1945,6 +1961,7 @@ int solve(const Call& q)
     }
     if (!q.Vin) return RMB_ERR_ARG;
     if (O->grid_ctas < 0 || O->barrier_timeout_ns < 0) return RMB_ERR_ARG;
+    if ((O->flags & RMB_FLAG_ASYNC) && M->format != RMB_CSR) return RMB_ERR_UNSUPPORTED;
     const Layout L = layout(M->n, b);
     if (!q.ws || ((uintptr_t)q.ws & 255)) return RMB_ERR_WORKSPACE;
     if (q.ws_bytes < L.total) return RMB_ERR_WORKSPACE;
@@ -2289,6 +2306,7 @@ int check_batch(const rmb_batch_item* items, int count, const rmb_opts* O)
 {
     if (!items || count < 1 || !O) return RMB_ERR_ARG;
     if (O->max_sweeps < 1 || !(O->eps >= 0.0) || std::isinf(O->eps) || O->start_sweep < 0) return RMB_ERR_ARG;
+    if (O->flags & RMB_FLAG_ASYNC) return RMB_ERR_UNSUPPORTED;
     for (int i = 0; i < count; ++i) {
         const int st = check_mdp(&items[i].mdp);
         if (st) return st;
