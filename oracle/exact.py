@@ -103,8 +103,10 @@ def policy_iteration(mdp, max_iters: int = 200):
     for _ in range(max_iters):
         J = policy_value(mdp, pi)
         TJ, new_pi, gap, Q = bellman_pass(mdp, J)
-        # keep the current action on exact ties so PI terminates
-        keep = Q[np.arange(mdp.n), pi] <= TJ
+        # keep the current action when it ties the minimum up to the rounding of the policy solve
+        # (symmetric moves give exact ties; an iterative solve can tip them either way and cycle)
+        tie = 1e-11 * max(1.0, float(np.max(np.abs(J))))
+        keep = Q[np.arange(mdp.n), pi] <= TJ + tie
         new_pi = np.where(keep, pi, new_pi).astype(np.int32)
         if np.array_equal(new_pi, pi):
             return J, pi, float(np.max(np.abs(TJ - J)))
