@@ -205,8 +205,9 @@ int rmb_validate(const rmb_mdp *mdp, void *workspace, size_t workspace_bytes, vo
  * Instead of a caller-provided workspace it uses one fixed scratch array of
  * RMB_NOALLOC_SCRATCH_BYTES (8 MiB) compiled into the library as a file-scope __device__ array;
  * every GPU that loads the library holds that array until the process exits.  A solve needs
- * rmb_workspace_bytes(mdp, opts) of scratch (about 8*n + 16*min(b,n) bytes, plus 4*n when a sweep
- * has 16 or more batches); larger problems are rejected with RMB_ERR_TOO_LARGE before anything is
+ * rmb_workspace_bytes(mdp, opts) of scratch (about 8*n + 16*min(b,n) bytes, plus 4*n when the
+ * permutation is precomputed: T = ceil(n/b) >= 16, or 2 <= T and n < T*65536); larger problems are
+ * rejected with RMB_ERR_TOO_LARGE before anything is
  * launched.  The call allocates nothing: no
  * cudaMalloc, no cudaFree, no allocating library routine, no CUDA events.
  *

@@ -24,6 +24,7 @@ import numpy as np
 __all__ = [
     "MDP", "dense_dirichlet", "csr_uniform_k", "batched_uneven", "random_values",
     "random_policy", "config1", "config2", "config3", "config4", "config5", "csr_ragged",
+    "maze_grid", "maze", "maze80", "maze100",
 ]
 
 
@@ -41,6 +42,7 @@ class MDP:
     prob: Optional[np.ndarray] = None          # float32 [nnz] (csr)
     logits: Optional[np.ndarray] = None        # float32 [nnz] when prob = softmax(logits)
     name: str = ""
+    meta: dict = dataclasses.field(default_factory=dict)   # generator extras (maze grid, goal state)
 
     @property
     def nnz(self) -> int:
@@ -281,3 +283,104 @@ def dense_dirichlet_device(n: int, m: int, alpha: float, gamma: float, seed: int
     else:
         cost = torch.rand(rows, generator=g, dtype=torch.float64, device=device).to(torch.float32)
     return P.reshape(n, m, n), cost
+
+
+# ---------------------------------------------------------------------------------------------
+# 2D-maze stand-ins (Sec. IV-A: an N x N maze with obstacles, 4 actions, every admissible
+# state-action-next-state triple has nonzero probability, unit cost except at the terminal state;
+# N = 80 and N = 100 leave 6166 and 9706 open cells).  The authors' maps are not available: the
+# walls here are seeded random segments, placed only where every open cell stays reachable.
+# ---------------------------------------------------------------------------------------------
+MAZE_MOVES = ((-1, 0), (0, 1), (1, 0), (0, -1))      # actions 0..3: up, right, down, left
+
+
+def maze_grid(N: int, n_open: int, seed: int = 0) -> np.ndarray:
+    """Boolean N x N grid (True = open) with exactly ``n_open`` open cells, all 4-connected.
+
+    Walls grow as straight segments of max(2, N//8)..max(2, N//2) cells from random cells in random
+    directions; a cell whose removal would split the open cells is skipped (the segment stops).
+    """
+    from scipy import ndimage
+
+    if not 1 <= n_open <= N * N:
+        raise ValueError("n_open must be in [1, N*N]")
+    g = _rng(seed)
+    grid = np.ones((N, N), dtype=bool)
+    walls = N * N - n_open
+    placed = 0
+    tries = 0
+    while placed < walls:
+        tries += 1
+        if tries > 100 * N * N:
+            raise RuntimeError("could not place the walls")
+        r, c = (int(x) for x in g.integers(0, N, size=2))
+        dr, dc = MAZE_MOVES[int(g.integers(0, 4))]
+        for _ in range(int(g.integers(max(2, N // 8), max(2, N // 2) + 1))):
+            if placed >= walls or not (0 <= r < N and 0 <= c < N) or not grid[r, c]:
+                break
+            grid[r, c] = False
+            if ndimage.label(grid)[1] != 1:
+                grid[r, c] = True
+                break
+            placed += 1
+            r, c = r + dr, c + dc
+    return grid
+
+
+def maze(N: int, n_open: int, gamma: float = 0.95, slip: float = 0.2, seed: int = 0, name: str = "") -> MDP:
+    """CSR MDP of an N x N maze with ``n_open`` open cells (states, row-major order).
+
+    The goal (terminal) is the open cell nearest the corner (N-1, N-1): absorbing, cost 0.  Every
+    other (state, action) pair costs 1.  Action a aims at the neighbour in direction a (or at the
+    cell itself when a wall or the border is there); the successors are the cell and its open
+    4-neighbours, the aimed one with probability 1 - slip and the others sharing slip evenly.
+    slip = 0 keeps only the aimed successor (a deterministic maze).
+    ``meta``: grid, goal (state index), cells (row, col of every state).
+    """
+    if not 0.0 <= slip < 1.0:
+        raise ValueError("slip must be in [0, 1)")
+    grid = maze_grid(N, n_open, seed)
+    cells = np.argwhere(grid)                       # row-major: state s is cells[s]
+    index = -np.ones((N, N), dtype=np.int64)
+    index[grid] = np.arange(len(cells))
+    corner = np.abs(cells - (N - 1)).sum(axis=1)
+    goal = int(np.argmin(corner))
+    m = 4
+    rows = len(cells) * m
+    row_ptr = np.zeros(rows + 1, dtype=np.int64)
+    cols: List[np.ndarray] = []
+    probs: List[np.ndarray] = []
+    cost = np.ones(rows, dtype=np.float32)
+    for s, (r, c) in enumerate(cells):
+        nb = []
+        for dr, dc in MAZE_MOVES:
+            rr, cc = r + dr, c + dc
+            ok = 0 <= rr < N and 0 <= cc < N and grid[rr, cc]
+            nb.append(int(index[rr, cc]) if ok else s)
+        support = np.array(sorted(set([s] + nb)), dtype=np.int32)
+        for a in range(m):
+            if s == goal:
+                col_a, p_a = np.array([s], np.int32), np.array([1.0])
+                cost[s * m + a] = 0.0
+            elif slip == 0.0 or len(support) == 1:
+                col_a, p_a = np.array([nb[a]], np.int32), np.array([1.0])
+            else:
+                p_a = np.where(support == nb[a], 1.0 - slip, slip / (len(support) - 1))
+                col_a = support
+            cols.append(col_a)
+            probs.append(p_a)
+            row_ptr[s * m + a + 1] = row_ptr[s * m + a] + len(col_a)
+    col = np.concatenate(cols).astype(np.int32)
+    prob = np.concatenate(probs).astype(np.float32)
+    return MDP(n=len(cells), m=m, gamma=gamma, fmt="csr", cost=cost, row_ptr=row_ptr, col=col, prob=prob,
+               name=name or f"maze{N}", meta={"grid": grid, "goal": goal, "cells": cells})
+
+
+def maze80(seed: int = 5, slip: float = 0.2) -> MDP:
+    """The N = 80 maze shape of Sec. IV-A: 6166 states, 4 actions, gamma 0.95."""
+    return maze(80, 6166, gamma=0.95, slip=slip, seed=seed, name="maze80")
+
+
+def maze100(seed: int = 6, slip: float = 0.2) -> MDP:
+    """The N = 100 maze shape of Sec. IV-A: 9706 states, 4 actions, gamma 0.95."""
+    return maze(100, 9706, gamma=0.95, slip=slip, seed=seed, name="maze100")

@@ -68,7 +68,7 @@ struct KP {
     int lps_all, lps_one;   // CSR: lanes sharing one state (all actions / one row)
     int nc_all, nc_one;     // CSR vectorised: float4 chunks per lane per state (0 = general loop)
     int k4_log2;            // CSR vectorised: log2(k/4)
-    int32_t* perm_buf;      // non-null when a sweep has >= 16 batches: sigma of the coming sweep
+    int32_t* perm_buf;      // non-null when sigma is precomputed (see use_perm_buf): sigma of the coming sweep
     int stage;              // dense: floats of V staged per chunk
     // buffers
     const float* Vin;
@@ -169,13 +169,56 @@ __device__ __forceinline__ Best csr_vec_state(const KP& p, int s, int pi_s, bool
     return best;
 }
 
-// Q-factors of one state on the generic CSR path (ragged rows): the whole warp walks each row.
+// Q-factors of one state on the generic CSR path (ragged rows).  The m rows of a state are
+// contiguous; when they hold at most 32 entries in all, lane e takes entry e of the state, a
+// segmented warp scan sums every row, and the row ends combine to the minimum (three dependent
+// loads per state).  With a policy (pi_s >= 0) only that row's lanes load, at the same lanes and
+// through the same scan, so T_pi and the Q-factor of the improvement pass round identically.
+// Otherwise the whole warp walks each row in turn.
 template <bool ARG>
 __device__ __forceinline__ Best csr_gen_state(const KP& p, int s, int pi_s, bool act,
                                               const float* __restrict__ A, int lane)
 {
     const int nrows = pi_s >= 0 ? 1 : p.m;
     const uint32_t nm1 = (uint32_t)(p.n - 1);
+    if (p.m < 32) {
+        const int64_t r0 = (int64_t)s * p.m;
+        long long rp = 0;
+        float c = kInf;
+        if (act && lane <= p.m) rp = __ldg(p.row_ptr + r0 + lane);   // lane l < m: start of row l; lane m: end
+        if (act && lane < p.m) c = __ldg(p.cost + r0 + lane);
+        const long long E0 = __shfl_sync(0xffffffffu, rp, 0);
+        const long long E1 = __shfl_sync(0xffffffffu, rp, p.m);
+        if (E1 - E0 <= 32) {
+            const long long nxt = __shfl_down_sync(0xffffffffu, rp, 1);
+            const int len = lane < p.m ? (int)(nxt - rp) : 0;
+            uint32_t starts = (act && len > 0) ? (1u << (int)(rp - E0)) : 0u;   // heads of non-empty rows
+            for (int off = 16; off > 0; off >>= 1) starts |= __shfl_xor_sync(0xffffffffu, starts, off);
+            int lo = 0, hi = (int)(E1 - E0);
+            if (pi_s >= 0) {
+                lo = (int)(__shfl_sync(0xffffffffu, rp, pi_s) - E0);
+                hi = (int)(__shfl_sync(0xffffffffu, rp, pi_s + 1) - E0);
+            }
+            float x = 0.f;
+            if (act && lane >= lo && lane < hi) {
+                const long long e = E0 + lane;
+                x = __ldcs(p.prob + e) * gather(A, __ldcs(p.col + e), nm1);
+            }
+            // inclusive scan within rows: add the value d lanes down unless a row starts in between
+            for (int d = 1; d < 32; d <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= d && ((starts >> (lane - d + 1)) & ((1u << d) - 1u)) == 0u) x += y;
+            }
+            const float sum = __shfl_sync(0xffffffffu, x, len > 0 ? (int)(nxt - E0) - 1 : 0);
+            Best cur = {kInf, 0x7fffffff, kInf};
+            if (act && (pi_s >= 0 ? lane == pi_s : lane < p.m)) {
+                cur.a = lane;
+                cur.q = (c == kInf) ? kInf : fmaf(p.gamma, len > 0 ? sum : 0.f, c);
+            }
+            for (int off = 16; off > 0; off >>= 1) cur = better(cur, shfl_xor_best<ARG>(cur, off));
+            return cur;
+        }
+    }
     Best best = {kInf, 0x7fffffff, kInf};
     for (int ai = 0; ai < nrows; ++ai) {
         const int a = pi_s >= 0 ? pi_s : ai;
@@ -1164,6 +1207,9 @@ struct Runner {
             publish(c, slot, acc, rs);
             if (!sync(12)) return false;
         }
+        // one batch (b >= n) is the Bellman operator T: every state reads old values only, so the
+        // order is immaterial and sigma is not evaluated (nor the position / value caches written)
+        const bool ordered = p.T > 1;
         for (int t = 0; t < (async ? 0 : p.T); ++t) {
             float* A = p.d[(cur + t) & 1];
             float* B = p.d[(cur + t + 1) & 1];
@@ -1177,7 +1223,9 @@ struct Runner {
                 c_s = ld_l2(p.S[(t - 1) & 1] + c0);
                 c_v = ld_l2(p.W[(t - 1) & 1] + c0);
             }
-            if (!batch<KIND>(A, B, t * p.b, len, &K, p.S[t & 1], p.W[t & 1], acc)) return false;
+            if (!batch<KIND>(A, B, t * p.b, len, ordered ? &K : nullptr, ordered ? p.S[t & 1] : nullptr,
+                             ordered ? p.W[t & 1] : nullptr, acc))
+                return false;
             if (c_s >= 0) st_l2(B + c_s, c_v);
             if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B, gthreads());
             if (t == p.T - 1) publish(c, slot, acc, rs);
@@ -1743,8 +1791,18 @@ struct Layout {
     bool perm_buf;
 };
 
-// A sweep with at least this many batches precomputes its permutation into the workspace.
+// A sweep with at least this many batches precomputes its permutation into the workspace ...
 constexpr int64_t kPermBufMinBatches = 16;
+// ... and so does one with 2..15 batches when n < batches * 65536: evaluating sigma for all n
+// positions once per sweep (about n / 65536 evaluations per thread of a full grid) then costs less
+// than one evaluation, with its cycle-walking tail, on the path of every batch.
+constexpr int64_t kPermBufPerBatch = 65536;
+
+bool use_perm_buf(int64_t n, int64_t b)
+{
+    const int64_t T = (n + b - 1) / b;
+    return T >= kPermBufMinBatches || (T >= 2 && n < T * kPermBufPerBatch);
+}
 
 Layout layout(int64_t n, int64_t b)
 {
@@ -1759,7 +1817,7 @@ Layout layout(int64_t n, int64_t b)
     L.w0 = L.s1 + bb;
     L.w1 = L.w0 + bb;
     L.pb = L.w1 + bb;
-    L.perm_buf = (n + b - 1) / b >= kPermBufMinBatches;
+    L.perm_buf = use_perm_buf(n, b);
     L.total = L.pb + (L.perm_buf ? nb : 0);
     return L;
 }

@@ -149,11 +149,19 @@ def test_workspace_size_formula(L):
     o = _opts(b=64)
     nb = L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o))
     # control block + two value buffers + two position caches + two value caches, 256-byte aligned,
-    # + the precomputed permutation when a sweep has >= 16 batches (here 16)
+    # + the precomputed permutation when T = ceil(n/b) >= 16, or 2 <= T and n < T * 65536
     assert nb == 256 + 2 * 4096 + 4 * 256 + 4096
-    o.batch = 67            # 15 batches: evaluated on the fly
-    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 256 + 2 * 4096 + 4 * 512
-    o.batch = 5000          # b > n means b = n
+    o.batch = 67            # 15 batches, n small: precomputed too
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 256 + 2 * 4096 + 4 * 512 + 4096
+    o.batch = 5000          # b > n means b = n: one batch, no permutation
     assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 256 + 6 * 4096
+    big = _fake_mdp(n=1 << 20)
+    o.batch = 1 << 18       # 4 batches of a large MDP: evaluated on the fly
+    assert L.rmb_workspace_bytes(ctypes.byref(big), ctypes.byref(o)) == 256 + 2 * (4 << 20) + 4 * (1 << 20)
+    o.batch = 1 << 16       # 16 batches
+    assert L.rmb_workspace_bytes(ctypes.byref(big), ctypes.byref(o)) == 256 + 2 * (4 << 20) + 4 * (1 << 18) + (4 << 20)
+    o.batch = 70000         # 15 batches and n >= 15 * 65536: on the fly
+    bb = (70000 * 4 + 255) // 256 * 256
+    assert L.rmb_workspace_bytes(ctypes.byref(big), ctypes.byref(o)) == 256 + 2 * (4 << 20) + 4 * bb
     d.gamma = 2.0
     assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 0
