@@ -7,7 +7,8 @@ with it; the two meet only through the seeded generators of ``mdpgen``.
 Two parts:
   * ``oracle.c`` (loaded here with ctypes): the mini-batch operator B_b / B_{pi,b} of eqs. (11)-(12)
     with the per-sweep random re-indexing of Sec. III-A, MB-VI, MB-MPI (Alg. 1), the greedy pass,
-    Philox4x32-10 and the Feistel permutation, all in FP64;
+    Philox4x32-10 and the Feistel permutation, batch selection with replacement (uniform or by
+    integer weights, the Sec. V extension), all in FP64;
   * ``exact.py``: closed forms from linear algebra (policy values by direct solve, brute force over
     all deterministic policies, optimality certificates) used to pin the iterative part.
 """
@@ -55,6 +56,12 @@ def lib():
         L.orc_mbvi.restype = i64
         L.orc_mpi.argtypes = [P(_OrcMDP), i64, i32, u64, i64, f64, i64, vp, vp, vp, vp]
         L.orc_mpi.restype = i64
+        L.orc_sweep_order.argtypes = [i64, u64, u64, i32, vp, vp]
+        L.orc_sweep_order.restype = ctypes.c_int
+        L.orc_mbvi_select.argtypes = [P(_OrcMDP), vp, i64, u64, i64, f64, i64, i32, vp, vp, vp, vp, vp]
+        L.orc_mbvi_select.restype = i64
+        L.orc_mpi_select.argtypes = [P(_OrcMDP), i64, i32, u64, i64, f64, i64, i32, vp, vp, vp, vp, vp]
+        L.orc_mpi_select.restype = i64
         L.orc_bellman_T.argtypes = [P(_OrcMDP), vp, vp]
         L.orc_gauss_seidel_F.argtypes = [P(_OrcMDP), vp, vp]
         L.orc_num_threads.restype = ctypes.c_int
@@ -134,6 +141,27 @@ def perm_at(n: int, seed: int, sweep: int, p: int) -> int:
     return int(lib().orc_perm(int(n), int(seed), int(sweep), int(p)))
 
 
+SELECT_PERMUTATION, SELECT_UNIFORM, SELECT_WEIGHTED = 0, 1, 2
+
+
+def _weights(select: int, weights, n: int):
+    if select != SELECT_WEIGHTED:
+        return None
+    w = np.ascontiguousarray(weights, dtype=np.uint32)
+    if w.shape != (n,):
+        raise ValueError("weights must be uint32 [n]")
+    return w
+
+
+def sweep_order(n: int, seed: int, sweep: int, select: int = 0, weights=None) -> np.ndarray:
+    """States of the n positions of one sweep: sigma (select 0) or draws with replacement (1, 2)."""
+    out = np.empty(int(n), dtype=np.int64)
+    w = _weights(select, weights, int(n))
+    if lib().orc_sweep_order(int(n), int(seed), int(sweep), int(select), _ptr(w), _ptr(out)) != 0:
+        raise ValueError("bad select or zero total weight")
+    return out
+
+
 # ----------------------------------------------------------------------------------------------
 # Operators and schemes
 # ----------------------------------------------------------------------------------------------
@@ -166,10 +194,12 @@ def mb_apply(mdp, J: np.ndarray, b: int, seed: int, sweep: int, pi: Optional[np.
 
 
 def mbvi(mdp, b: int, seed: int, eps: float = 1e-6, max_sweeps: int = 100000, V0=None,
-         start_sweep: int = 0, pi: Optional[np.ndarray] = None, traj: bool = False):
+         start_sweep: int = 0, pi: Optional[np.ndarray] = None, traj: bool = False, select: int = 0,
+         weights=None):
     """MB-VI (pi None) or mini-batch policy evaluation (pi given) until delta <= eps.
 
-    Returns dict(V, sweeps, deltas[, traj]).
+    select 1 / 2: batches drawn with replacement (uniform / by the uint32 weights); the stop then
+    also needs the full residual <= eps.  Returns dict(V, sweeps, deltas, resid[, traj]).
     """
     B = _bind(mdp)
     n = mdp.n
@@ -177,9 +207,14 @@ def mbvi(mdp, b: int, seed: int, eps: float = 1e-6, max_sweeps: int = 100000, V0
     deltas = np.zeros(int(max_sweeps), dtype=np.float64)
     T = np.zeros((int(max_sweeps), n), dtype=np.float64) if traj else None
     pi_c = None if pi is None else np.ascontiguousarray(pi, dtype=np.int32)
-    k = lib().orc_mbvi(B.ref, _ptr(pi_c), int(b), int(seed), int(start_sweep), float(eps),
-                       int(max_sweeps), _ptr(V), _ptr(deltas), _ptr(T))
-    out = {"V": V, "sweeps": int(k), "deltas": deltas[:k]}
+    w = _weights(select, weights, n)
+    resid = ctypes.c_double(0.0)
+    k = lib().orc_mbvi_select(B.ref, _ptr(pi_c), int(b), int(seed), int(start_sweep), float(eps),
+                              int(max_sweeps), int(select), _ptr(w), _ptr(V), _ptr(deltas), _ptr(T),
+                              ctypes.byref(resid))
+    if k < 0:
+        raise ValueError("bad select or zero total weight")
+    out = {"V": V, "sweeps": int(k), "deltas": deltas[:k], "resid": float(resid.value)}
     if traj:
         out["traj"] = T[:k]
     return out
@@ -191,7 +226,7 @@ def eval_policy(mdp, pi, b: int, seed: int, eps: float = 1e-6, max_sweeps: int =
 
 
 def mpi(mdp, b: int, K: int, seed: int, eps: float = 1e-6, max_iters: int = 100000, V0=None,
-        start_sweep: int = 0):
+        start_sweep: int = 0, select: int = 0, weights=None):
     """MB-MPI (Alg. 1 with B_{pi,b}); returns dict(V, pi, iters, sweeps, resid)."""
     B = _bind(mdp)
     n = mdp.n
@@ -199,8 +234,11 @@ def mpi(mdp, b: int, K: int, seed: int, eps: float = 1e-6, max_iters: int = 1000
     pi = np.zeros(n, dtype=np.int32)
     sw = ctypes.c_int64(0)
     res = np.zeros(int(max_iters), dtype=np.float64)
-    it = lib().orc_mpi(B.ref, int(b), int(K), int(seed), int(start_sweep), float(eps), int(max_iters),
-                       _ptr(V), _ptr(pi), ctypes.byref(sw), _ptr(res))
+    w = _weights(select, weights, n)
+    it = lib().orc_mpi_select(B.ref, int(b), int(K), int(seed), int(start_sweep), float(eps), int(max_iters),
+                              int(select), _ptr(w), _ptr(V), _ptr(pi), ctypes.byref(sw), _ptr(res))
+    if it < 0:
+        raise ValueError("bad select or zero total weight")
     return {"V": V, "pi": pi, "iters": int(it), "sweeps": int(sw.value), "resid": res[:it]}
 
 

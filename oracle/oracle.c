@@ -16,7 +16,10 @@
  * policies with direct linear solves, closed-form policy values, the monotonicity / shift /
  * contraction / fixed-point properties (Sec. III-B.1), the batch-size comparison theorem and its
  * corollary (Sec. III-B.2), the set-based definition of M_m(i) (eq. M(i) definition) and the
- * b=n / b=1 reductions (Sec. III-A).
+ * b=n / b=1 reductions (Sec. III-A).  The batch selection with replacement (Sec. V extension) is
+ * pinned against its draw rule written with Python integers, constant weights against uniform
+ * draws, draw frequencies, a batch-by-batch definition with repeated states, and J* through the
+ * full-residual stop rule.
  */
 #include <math.h>
 #include <stdint.h>
@@ -125,6 +128,72 @@ void orc_perm_all(int64_t n, uint64_t seed, uint64_t sweep, int64_t *out)
 }
 
 /* ------------------------------------------------------------------------------------------ *
+ * Batch selection with replacement (Sec. V names sampling with replacement and non-uniform /
+ * importance-sampled selection as extensions; the paper gives no rule, the one below is ours).
+ * Position p of sweep k draws x = Philox4x32-10(ctr = {p, 2^31, k_lo, k_hi}, key = {seed_lo,
+ * seed_hi}) (the second counter word never takes the Feistel round numbers 0..7) and reads the
+ * 64-bit integer u = x0 * 2^32 + x1.  Then, in exact integer arithmetic:
+ *   select 1 (uniform):  state = floor(u * n / 2^64);
+ *   select 2 (weighted, integer weights w with W = sum w > 0): r = floor(u * W / 2^64) and
+ *     state = the smallest s with w_0 + ... + w_s > r, so P(state = s) = w_s / W up to 2^-64.
+ * ------------------------------------------------------------------------------------------ */
+static uint64_t draw_word(uint64_t seed, uint64_t sweep, int64_t p)
+{
+    uint32_t key[2] = { (uint32_t)seed, (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { (uint32_t)p, 0x80000000u, (uint32_t)sweep, (uint32_t)(sweep >> 32) };
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return ((uint64_t)out[0] << 32) | out[1];
+}
+
+/* cumulative weights: cum[s] = w_0 + ... + w_s (plain running sum) */
+static uint64_t *cumulative(int64_t n, const uint32_t *w)
+{
+    uint64_t *cum = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)n);
+    uint64_t run = 0;
+    for (int64_t s = 0; s < n; ++s) {
+        run += w[s];
+        cum[s] = run;
+    }
+    return cum;
+}
+
+/* the state of position p; cum = NULL for select 1 */
+static int64_t draw_state(int64_t n, uint64_t seed, uint64_t sweep, int64_t p, const uint64_t *cum)
+{
+    unsigned __int128 u = draw_word(seed, sweep, p);
+    if (!cum) return (int64_t)((u * (unsigned __int128)(uint64_t)n) >> 64);
+    uint64_t r = (uint64_t)((u * (unsigned __int128)cum[n - 1]) >> 64);
+    /* smallest s with cum[s] > r (cum is nondecreasing and cum[n-1] > r) */
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (cum[mid] > r) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+/* processing order of one sweep: sigma (select 0) or n draws (select 1, 2); weights for 2 */
+int orc_sweep_order(int64_t n, uint64_t seed, uint64_t sweep, int32_t select, const uint32_t *weights,
+                    int64_t *out)
+{
+    if (select == 0) {
+        orc_perm_all(n, seed, sweep, out);
+        return 0;
+    }
+    if ((select != 1 && select != 2) || n < 1) return -1;
+    uint64_t *cum = NULL;
+    if (select == 2) {
+        cum = cumulative(n, weights);
+        if (cum[n - 1] == 0) { free(cum); return -1; }
+    }
+    for (int64_t p = 0; p < n; ++p) out[p] = draw_state(n, seed, sweep, p, cum);
+    free(cum);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------------ *
  * Q-factor of one state-action pair at a value function J (the bracket of eqs. (6)-(7), the
  * Bellman operators T_mu and T):  g(i,u) + alpha * sum_j p_ij(u) J(j).
  * ------------------------------------------------------------------------------------------ */
@@ -194,11 +263,10 @@ double orc_greedy(const orc_mdp *M, const double *V, double *TV, int32_t *pi, do
  * perm: caller-provided scratch of n entries (filled here).  W: scratch of b doubles.
  * Returns max_s |V_new(s) - V_old(s)|.
  * ------------------------------------------------------------------------------------------ */
-double orc_mb_apply(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, uint64_t sweep,
-                    double *V, int64_t *perm, double *W)
+/* one sweep over a given processing order (n positions in batches of b; entries may repeat) */
+static double apply_order(const orc_mdp *M, const int32_t *pi, int64_t b, const int64_t *perm, double *V, double *W)
 {
     int64_t n = M->n;
-    orc_perm_all(n, seed, sweep, perm);
     double delta = 0.0;
     for (int64_t start = 0; start < n; start += b) {
         int64_t len = (n - start < b) ? (n - start) : b;
@@ -220,26 +288,74 @@ double orc_mb_apply(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t see
     return delta;
 }
 
+double orc_mb_apply(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, uint64_t sweep,
+                    double *V, int64_t *perm, double *W)
+{
+    orc_perm_all(M->n, seed, sweep, perm);
+    return apply_order(M, pi, b, perm, V, W);
+}
+
+/* ||T V - V||_inf (pi NULL) or ||T_pi V - V||_inf over all states */
+static double full_residual(const orc_mdp *M, const int32_t *pi, const double *V)
+{
+    double r = 0.0;
+    for (int64_t s = 0; s < M->n; ++s) {
+        double t = pi ? orc_q(M, s, pi[s], V) : backup_min(M, s, V, NULL, NULL);
+        double d = fabs(t - V[s]);
+        if (d > r || isnan(d)) r = d;
+    }
+    return r;
+}
+
 /* ------------------------------------------------------------------------------------------ *
  * MB-VI (Sec. III-B: B_b in place of T in value iteration).  Sweep k = start_sweep, start_sweep+1,
  * ... applies B_b with sigma_{seed,k}; stops after the first sweep with delta_k <= eps or after
  * max_sweeps sweeps.  delta_trace[j] (optional) = delta of the j-th sweep; V_traj (optional,
  * [max_sweeps*n]) = V after each sweep.  Returns the number of sweeps done.
  * ------------------------------------------------------------------------------------------ */
+int64_t orc_mbvi_select(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, int64_t start_sweep,
+                        double eps, int64_t max_sweeps, int32_t select, const uint32_t *weights, double *V,
+                        double *delta_trace, double *V_traj, double *resid_out);
+
 int64_t orc_mbvi(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, int64_t start_sweep,
                  double eps, int64_t max_sweeps, double *V, double *delta_trace, double *V_traj)
+{
+    return orc_mbvi_select(M, pi, b, seed, start_sweep, eps, max_sweeps, 0, NULL, V, delta_trace, V_traj, NULL);
+}
+
+/* ------------------------------------------------------------------------------------------ *
+ * MB-VI / evaluation with a batch-selection rule (select 0: sigma, the paper's method; 1, 2: draws
+ * with replacement as defined above).  With draws a sweep's change covers only the states drawn,
+ * so a sweep with delta <= eps is followed by the full residual ||TV - V||_inf (||T_pi V - V||_inf)
+ * and the solve stops only when that is <= eps too.  *resid_out (optional) = the last full residual
+ * (select 1, 2) or delta (select 0).  Returns sweeps done, or -1 on a bad select / zero weights.
+ * ------------------------------------------------------------------------------------------ */
+int64_t orc_mbvi_select(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, int64_t start_sweep,
+                        double eps, int64_t max_sweeps, int32_t select, const uint32_t *weights, double *V,
+                        double *delta_trace, double *V_traj, double *resid_out)
 {
     int64_t n = M->n;
     int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
     double *W = (double *)malloc(sizeof(double) * (size_t)(b < n ? b : n));
     int64_t done = 0;
+    double resid = 0.0;
     for (int64_t j = 0; j < max_sweeps; ++j) {
-        double delta = orc_mb_apply(M, pi, b, seed, (uint64_t)(start_sweep + j), V, perm, W);
+        if (orc_sweep_order(n, seed, (uint64_t)(start_sweep + j), select, weights, perm) != 0) {
+            done = -1;
+            break;
+        }
+        double delta = apply_order(M, pi, b, perm, V, W);
         if (delta_trace) delta_trace[j] = delta;
         if (V_traj) memcpy(V_traj + j * n, V, sizeof(double) * (size_t)n);
         done = j + 1;
-        if (delta <= eps) break;
+        resid = delta;
+        if (delta <= eps) {
+            if (select == 0) break;
+            resid = full_residual(M, pi, V);
+            if (resid <= eps) break;
+        }
     }
+    if (resid_out) *resid_out = resid;
     free(perm);
     free(W);
     return done;
@@ -254,9 +370,22 @@ int64_t orc_mbvi(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, 
  * resid_trace[it] (optional) = residual of outer iteration it.  Returns outer iterations done
  * (greedy passes); *sweeps_out = evaluation sweeps done.
  * ------------------------------------------------------------------------------------------ */
+int64_t orc_mpi_select(const orc_mdp *M, int64_t b, int32_t K, uint64_t seed, int64_t start_sweep,
+                       double eps, int64_t max_iters, int32_t select, const uint32_t *weights, double *V,
+                       int32_t *pi, int64_t *sweeps_out, double *resid_trace);
+
 int64_t orc_mpi(const orc_mdp *M, int64_t b, int32_t K, uint64_t seed, int64_t start_sweep,
                 double eps, int64_t max_iters, double *V, int32_t *pi, int64_t *sweeps_out,
                 double *resid_trace)
+{
+    return orc_mpi_select(M, b, K, seed, start_sweep, eps, max_iters, 0, NULL, V, pi, sweeps_out, resid_trace);
+}
+
+/* MB-MPI whose evaluation sweeps use a batch-selection rule (select 0, 1, 2 as above); the stop
+   test is the improvement pass's full residual either way.  Returns -1 on a bad select. */
+int64_t orc_mpi_select(const orc_mdp *M, int64_t b, int32_t K, uint64_t seed, int64_t start_sweep,
+                       double eps, int64_t max_iters, int32_t select, const uint32_t *weights, double *V,
+                       int32_t *pi, int64_t *sweeps_out, double *resid_trace)
 {
     int64_t n = M->n;
     int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -268,7 +397,12 @@ int64_t orc_mpi(const orc_mdp *M, int64_t b, int32_t K, uint64_t seed, int64_t s
         it++;
         if (res <= eps || it >= max_iters) break;
         for (int32_t j = 0; j < K; ++j) {
-            orc_mb_apply(M, pi, b, seed, (uint64_t)sweep, V, perm, W);
+            if (orc_sweep_order(n, seed, (uint64_t)sweep, select, weights, perm) != 0) {
+                free(perm);
+                free(W);
+                return -1;
+            }
+            apply_order(M, pi, b, perm, V, W);
             sweep++;
         }
     }

@@ -385,3 +385,116 @@ def test_greedy_ties_resolve_to_lowest_action():
     assert np.all(pi == 1) and np.all(gap == 0)
     r = oracle.mpi(mdp, 7, K=3, seed=2, eps=1e-10, max_iters=1000)
     assert np.all(r["pi"] == 1)
+
+
+# ----------------------------------------------------------------------------------------------
+# Batch selection with replacement (the extension of Sec. V): uniform draws and draws by integer
+# weights, pinned against the draw rule written out with Python integers, against each other, by
+# frequency, against the batch-by-batch definition, and against J* through the stop rule.
+# ----------------------------------------------------------------------------------------------
+def _draws_by_definition(n, seed, sweep, select, weights=None):
+    """u = x0 * 2^32 + x1 of Philox4x32-10(ctr = {p, 2^31, k_lo, k_hi}, key = {seed_lo, seed_hi});
+    uniform: floor(u n / 2^64); weighted: r = floor(u W / 2^64), the first s whose cumulative
+    weight exceeds r."""
+    import bisect
+    import itertools
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    cum = list(itertools.accumulate(int(w) for w in weights)) if select == 2 else None
+    out = []
+    for p in range(n):
+        x = oracle.philox4x32_10([p, 1 << 31, sweep & 0xFFFFFFFF, sweep >> 32], key)
+        u = (int(x[0]) << 32) | int(x[1])
+        if select == 1:
+            out.append((u * n) >> 64)
+        else:
+            out.append(bisect.bisect_right(cum, (u * cum[-1]) >> 64))
+    return np.array(out, dtype=np.int64)
+
+
+def test_draws_follow_their_definition():
+    g = np.random.default_rng(5)
+    for n, seed, sweep in ((1, 3, 0), (7, 12345, 2), (300, 2**40 + 7, 2**33 + 1)):
+        assert np.array_equal(oracle.sweep_order(n, seed, sweep, 1), _draws_by_definition(n, seed, sweep, 1))
+        w = g.integers(0, 50, size=n).astype(np.uint32)
+        w[0] = max(int(w[0]), 1)
+        got = oracle.sweep_order(n, seed, sweep, 2, w)
+        assert np.array_equal(got, _draws_by_definition(n, seed, sweep, 2, w))
+        assert (w[got] > 0).all()
+
+
+def test_constant_weights_reproduce_uniform_draws():
+    # floor(floor(u n c / 2^64) / c) = floor(u n / 2^64): any constant weight gives the uniform draws
+    for n in (1, 7, 1000):
+        for c in (1, 3, (2**32 - 1) // n):
+            w = np.full(n, c, dtype=np.uint32)
+            for sweep in (0, 5):
+                assert np.array_equal(oracle.sweep_order(n, 99, sweep, 2, w), oracle.sweep_order(n, 99, sweep, 1))
+
+
+def test_weighted_draw_frequencies():
+    w = np.arange(8, dtype=np.uint32) * 3                  # state 0 has weight 0
+    counts = np.zeros(8)
+    for sweep in range(500):
+        counts += np.bincount(oracle.sweep_order(8, 4242, sweep, 2, w), minlength=8)
+    assert counts[0] == 0
+    expect = counts.sum() * w[1:] / w.sum()
+    chi2 = float(((counts[1:] - expect) ** 2 / expect).sum())
+    assert chi2 < 22.46                                      # 6 dof, p = 0.001
+    u = np.zeros(8)
+    for sweep in range(500):
+        u += np.bincount(oracle.sweep_order(8, 4242, sweep, 1), minlength=8)
+    assert float(((u - 500) ** 2 / 500).sum()) < 24.32       # 7 dof, p = 0.001
+
+
+def _definition_draws(mdp, J, b, order):
+    """One sweep over an order with repeats: batch by batch, every state of the batch takes
+    min_a [g + gamma sum_j p_j V(j)] at the values before the batch, then the batch writes."""
+    V = [float(x) for x in J]
+    n, m = mdp.n, mdp.m
+    for t0 in range(0, n, b):
+        new = {}
+        for s in (int(x) for x in order[t0:t0 + b]):
+            vals = []
+            for a in range(m):
+                r = s * m + a
+                g = float(mdp.cost[r])
+                if np.isinf(g):
+                    vals.append(np.inf)
+                    continue
+                if mdp.fmt == "dense":
+                    succ = [(j, float(mdp.P[s, a, j])) for j in range(n)]
+                else:
+                    succ = [(int(mdp.col[e]), float(mdp.prob[e])) for e in range(mdp.row_ptr[r], mdp.row_ptr[r + 1])]
+                vals.append(g + sum(mdp.gamma * p * V[j] for j, p in succ))
+            new[s] = min(vals)
+        for s, v in new.items():
+            V[s] = v
+    return np.array(V)
+
+
+@pytest.mark.parametrize("idx", [0, 1, 6])
+def test_with_replacement_sweep_matches_definition(idx):
+    mdp = _tiny_mdps()[idx]
+    J = mdpgen.random_values(mdp.n, seed=idx).astype(np.float64)
+    w = (np.arange(mdp.n, dtype=np.uint32) % 3) + 1
+    for b in range(1, mdp.n + 1):
+        for select in (1, 2):
+            for sweep in (0, 4):
+                order = oracle.sweep_order(mdp.n, 77, sweep, select, w)
+                r = oracle.mbvi(mdp, b, 77, eps=0.0, max_sweeps=1, V0=J, start_sweep=sweep, select=select,
+                                weights=w)
+                assert np.allclose(r["V"], _definition_draws(mdp, J, b, order), rtol=0, atol=1e-12)
+
+
+def test_with_replacement_converges_under_the_stop_rule():
+    mdp = mdpgen.csr_uniform_k(300, 4, 8, gamma=0.9, seed=13)
+    jstar, _, _ = exact.policy_iteration(mdp)
+    w = mdpgen._rng(3).integers(1, 20, size=mdp.n).astype(np.uint32)
+    for select in (1, 2):
+        for b in (1, 16, 300):
+            r = oracle.mbvi(mdp, b, 5, eps=1e-9, max_sweeps=100000, select=select, weights=w)
+            resid = float(np.max(np.abs(exact.bellman_pass(mdp, r["V"])[0] - r["V"])))
+            assert resid <= 1e-9 and abs(resid - r["resid"]) < 1e-12
+            assert np.max(np.abs(r["V"] - jstar)) <= 0.9 / 0.1 * resid + 1e-12
+        m = oracle.mpi(mdp, 16, K=5, seed=2, eps=1e-10, select=select, weights=w)
+        assert m["resid"][-1] <= 1e-10 and np.max(np.abs(m["V"] - jstar)) < 1e-8

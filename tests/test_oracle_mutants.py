@@ -32,8 +32,13 @@ MUTANTS = {
                                    "uint64_t prod0 = (uint64_t)PHILOX_M1 * (uint64_t)x0;"),
     "argmin_ties_to_highest": ("if (q < best) { second = best; best = q; ba = a; }",
                                "if (q <= best) { second = best; best = q; ba = a; }"),
-    "mpi_evaluates_wrong_policy_rows": ("orc_mb_apply(M, pi, b, seed, (uint64_t)sweep, V, perm, W);",
-                                        "orc_mb_apply(M, NULL, b, seed, (uint64_t)sweep, V, perm, W);"),
+    "mpi_evaluates_wrong_policy_rows": ("            apply_order(M, pi, b, perm, V, W);\n            sweep++;",
+                                        "            apply_order(M, NULL, b, perm, V, W);\n            sweep++;"),
+    "weighted_search_off_by_one": ("if (cum[mid] > r) hi = mid;", "if (cum[mid] >= r) hi = mid;"),
+    "draws_reuse_the_feistel_stream": ("uint32_t ctr[4] = { (uint32_t)p, 0x80000000u,", "uint32_t ctr[4] = { (uint32_t)p, 0u,"),
+    "weights_ignored": ("        run += w[s];", "        run += 1;"),
+    "stop_without_full_residual": ("            resid = full_residual(M, pi, V);\n            if (resid <= eps) break;",
+                                   "            break;"),
     "delta_not_a_change": ("double d = fabs(W[i] - V[s]);", "double d = fabs(W[i]);"),
 }
 
@@ -52,6 +57,10 @@ PINS = [
     T.test_mpi_first_outer_iteration_closed_form,
     T.test_mpi_matches_policy_iteration,
     T.test_greedy_ties_resolve_to_lowest_action,
+    T.test_draws_follow_their_definition,
+    T.test_constant_weights_reproduce_uniform_draws,
+    lambda: T.test_with_replacement_sweep_matches_definition(1),
+    T.test_with_replacement_converges_under_the_stop_rule,
 ]
 
 
@@ -76,7 +85,8 @@ def test_pins_catch_planted_mistake(name, monkeypatch):
         mut = ctypes.CDLL(so)
         for fn in ("orc_philox4x32_10", "orc_perm", "orc_perm_all", "orc_perm_half_bits", "orc_q",
                    "orc_greedy", "orc_mb_apply", "orc_mbvi", "orc_mpi", "orc_bellman_T",
-                   "orc_gauss_seidel_F", "orc_num_threads"):
+                   "orc_gauss_seidel_F", "orc_num_threads", "orc_sweep_order", "orc_mbvi_select",
+                   "orc_mpi_select"):
             f, g = getattr(mut, fn), getattr(real, fn)
             f.argtypes, f.restype = g.argtypes, g.restype
         monkeypatch.setattr(oracle, "_LIB", mut)
