@@ -96,7 +96,34 @@ typedef struct {
     int32_t flags;           /* RMB_FLAG_* */
     double *trace;           /* optional device [max_sweeps] doubles: per-sweep residual (VI /
                                 evaluation) or per-improvement residual (MPI); NULL = none */
+    int32_t select;          /* batch selection: RMB_SELECT_PERMUTATION (0, the paper's method),
+                                RMB_SELECT_UNIFORM or RMB_SELECT_WEIGHTED (with replacement) */
+    int32_t reserved_select;
+    const uint32_t *weights; /* RMB_SELECT_WEIGHTED: device [n] integer weights, sum > 0; else NULL */
 } rmb_opts;
+
+/*
+ * Batch selection with replacement (Sec. V proposes sampling with replacement and non-uniform /
+ * importance-sampled selection; the paper fixes no rule, this one is the library's).  A sweep is
+ * still n positions in batches of b, but position p of sweep k holds a drawn state instead of
+ * sigma_{seed,k}(p):  u = x0 * 2^32 + x1 of Philox4x32-10(ctr = {p, 2^31, k_lo, k_hi},
+ * key = {seed_lo, seed_hi}) (the Feistel rounds of sigma use counter words 0..7 there), then in
+ * exact integer arithmetic
+ *   RMB_SELECT_UNIFORM:  state = floor(u * n / 2^64);
+ *   RMB_SELECT_WEIGHTED: r = floor(u * W / 2^64) with W = sum of the weights, state = the smallest
+ *                        s with w_0 + ... + w_s > r (probability w_s / W; weight 0 = never drawn).
+ * A state drawn twice in one batch gets the same value twice; a state not drawn keeps its value.
+ * The sweep's change then covers only the drawn states, so a sweep whose change is <= eps is
+ * followed by a full Bellman pass, and the solve stops only if ||TV - V||_inf <= eps as well
+ * (stats->residual is that value).  Supported by rmb_vi, rmb_mpi (evaluation sweeps; MPI's stop
+ * test is its improvement pass) and rmb_vi_noalloc; rmb_eval_policy and the batched API return
+ * RMB_ERR_UNSUPPORTED.  A state drawn in two consecutive batches takes the later batch's value.
+ * Workspace: + 16*n bytes of batch marks when b < n, and for RMB_SELECT_WEIGHTED another 8*n bytes
+ * of cumulative weights (+ 8 per 8192 states).
+ */
+#define RMB_SELECT_PERMUTATION 0
+#define RMB_SELECT_UNIFORM 1
+#define RMB_SELECT_WEIGHTED 2
 
 /* Test-only fault injection: CTA 0 never arrives at the first grid-wide wait, so every wait runs
    out and the call must report RMB_ERR_BARRIER_TIMEOUT with the GPU context intact. */

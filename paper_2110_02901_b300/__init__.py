@@ -39,6 +39,7 @@ RMB_P_FP8E4M3 = 2
 RMB_FLAG_INJECT_BARRIER_STALL = 1
 RMB_FLAG_RAW_ROWS = 2
 RMB_FLAG_ASYNC = 4
+RMB_SELECT_PERMUTATION, RMB_SELECT_UNIFORM, RMB_SELECT_WEIGHTED = 0, 1, 2
 PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic", 3: "dense-tma"}
 
 
@@ -58,6 +59,7 @@ class rmb_opts(ctypes.Structure):
         ("eval_sweeps", ctypes.c_int32), ("validate", ctypes.c_int32),
         ("barrier_timeout_ns", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
         ("flags", ctypes.c_int32), ("trace", ctypes.c_void_p),
+        ("select", ctypes.c_int32), ("reserved_select", ctypes.c_int32), ("weights", ctypes.c_void_p),
     ]
 
 
@@ -209,6 +211,8 @@ class Opts:
     grid_ctas: int = 0
     flags: int = 0
     trace: object = None       # optional torch float64 CUDA tensor [max_sweeps]
+    select: int = 0            # RMB_SELECT_PERMUTATION / _UNIFORM / _WEIGHTED
+    weights: object = None     # RMB_SELECT_WEIGHTED: torch int32 (read as uint32) CUDA tensor [n]
 
     def desc(self) -> rmb_opts:
         o = rmb_opts()
@@ -217,6 +221,8 @@ class Opts:
         o.eval_sweeps, o.validate = int(self.eval_sweeps), int(bool(self.validate))
         o.barrier_timeout_ns, o.grid_ctas, o.flags = int(self.barrier_timeout_ns), int(self.grid_ctas), int(self.flags)
         o.trace = _ptr(self.trace)
+        o.select = int(self.select)
+        o.weights = _ptr(self.weights)
         return o
 
 

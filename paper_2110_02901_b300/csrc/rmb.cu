@@ -43,6 +43,10 @@ enum Path { PATH_DENSE = 0, PATH_CSR_VEC = 1, PATH_CSR_GEN = 2, PATH_DENSE_TMA =
 enum Kind { K_MIN = 0, K_POLICY = 1, K_GREEDY = 2 };
 
 constexpr int kCsrThreads = 512;
+// cumulative weights of RMB_SELECT_WEIGHTED: tiles of 8192 weights (1024 threads x 8)
+constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 8;
+constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanPer;
 constexpr int kDenseThreads = 256;
 constexpr int kDenseMaxM = 256;
 constexpr int kDenseMB = 8;               // actions accumulated per pass in the dense path
@@ -68,7 +72,10 @@ struct KP {
     int lps_all, lps_one;   // CSR: lanes sharing one state (all actions / one row)
     int nc_all, nc_one;     // CSR vectorised: float4 chunks per lane per state (0 = general loop)
     int k4_log2;            // CSR vectorised: log2(k/4)
-    int32_t* perm_buf;      // non-null when sigma is precomputed (see use_perm_buf): sigma of the coming sweep
+    int32_t* perm_buf;      // non-null when the order is precomputed (see use_perm_buf): that of the coming sweep
+    int select;             // RMB_SELECT_*: sigma, or draws with replacement (uniform / by weight)
+    const uint64_t* cdf;    // RMB_SELECT_WEIGHTED: cumulative weights [n] (in the workspace)
+    uint64_t* mark;         // draws with T >= 2: [2][n], mark[t & 1][s] = stamp of batch t if it updates s
     int stage;              // dense: floats of V staged per chunk
     // buffers
     const float* Vin;
@@ -1096,6 +1103,7 @@ struct Runner {
     static constexpr int NCO_ = NCO > 0 ? NCO : 1;
     Carry<NCA_> carry_a;    // prefetched first state of the next min-over-actions batch
     Carry<NCO_> carry_o;    // ... of the next policy-row batch
+    uint64_t wtot = 0;      // RMB_SELECT_WEIGHTED: sum of the weights (read at set-up)
 
     template <int KIND>
     __device__ bool batch(const float* A, float* B, int pos0, int len, const PermKey* K, int32_t* So, float* Wo,
@@ -1139,9 +1147,26 @@ struct Runner {
         if (KIND == K_MIN && NCA > 0) fast_prefetch_first<K_MIN, NCA_>(p, gv, p.lps_all, pos0, len, K, carry_a, &perm_ok);
     }
 
-    __device__ void copy_batch(const int32_t* S, const float* Wv, int len, float* B, size_t skip = 0)
+    __device__ void copy_batch(const int32_t* S, const float* Wv, int len, float* B, size_t skip = 0,
+                               uint64_t stamp = 0, const uint64_t* mk = nullptr)
     {
-        for (size_t i = gtid() + skip; i < (size_t)len; i += gthreads()) st_l2(B + ld_l2(S + i), ld_l2(Wv + i));
+        for (size_t i = gtid() + skip; i < (size_t)len; i += gthreads()) {
+            const int s = ld_l2(S + i);
+            if (stamp && ld_l2(mk + s) == stamp) continue;   // the current batch updates s itself
+            st_l2(B + s, ld_l2(Wv + i));
+        }
+    }
+
+    // Draws with replacement can put a state in two consecutive batches t and t+1; batch t+1 then
+    // writes its own value of s into the buffer that also receives batch t's values, so that copy
+    // must skip s.  The states of batch t+1 are marked during batch t (before its barrier), in the
+    // other half of the mark array than the one batch t's copy is reading.
+    __device__ void mark_batch(const PermKey& K, int pos0, int len, uint64_t stamp, uint64_t* mk)
+    {
+        bool ok = true;
+        for (size_t i = gtid(); i < (size_t)len; i += gthreads())
+            st_l2(mk + state_at((uint32_t)(pos0 + (int)i), K, &ok), stamp);
+        if (!ok) perm_ok = false;
     }
 
     // Re-centre between sweeps when the midpoint of the values moved by more than a quarter of
@@ -1168,17 +1193,20 @@ struct Runner {
         K.s_lo = (uint32_t)(unsigned long long)k;
         K.s_hi = (uint32_t)((unsigned long long)k >> 32);
         K.buf = nullptr;
+        K.select = (uint32_t)p.select;
+        K.wtot = wtot;
+        K.cdf = p.cdf;
         return K;
     }
 
-    // sigma of sweep k for every position, by the whole grid, into the permutation buffer (done in a
-    // phase that ends with a grid-wide barrier, before sweep k starts)
+    // the order of sweep k (sigma or the draws) for every position, by the whole grid, into the
+    // order buffer (done in a phase that ends with a grid-wide barrier, before sweep k starts)
     __device__ void compute_perm(long long k)
     {
         if (!p.perm_buf) return;
         const PermKey K = key_for(k);
         for (size_t i = gtid(); i < (size_t)p.n; i += gthreads())
-            st_l2(p.perm_buf + i, (int)perm_at((uint32_t)i, K, &perm_ok));
+            st_l2(p.perm_buf + i, order_at((uint32_t)i, K, &perm_ok));
     }
 
     // One sweep of B_b (KIND K_MIN) or B_{pi,b} (K_POLICY).  Returns false on failure; sets stop.
@@ -1207,9 +1235,10 @@ struct Runner {
             publish(c, slot, acc, rs);
             if (!sync(12)) return false;
         }
-        // one batch (b >= n) is the Bellman operator T: every state reads old values only, so the
-        // order is immaterial and sigma is not evaluated (nor the position / value caches written)
-        const bool ordered = p.T > 1;
+        // one batch (b >= n) of sigma is the Bellman operator T: every state reads old values only,
+        // so the order is immaterial and sigma is not evaluated (nor the position / value caches
+        // written).  Draws with replacement choose which states update, so they are always taken.
+        const bool ordered = p.T > 1 || p.select != RMB_SELECT_PERMUTATION;
         for (int t = 0; t < (async ? 0 : p.T); ++t) {
             float* A = p.d[(cur + t) & 1];
             float* B = p.d[(cur + t + 1) & 1];
@@ -1223,11 +1252,17 @@ struct Runner {
                 c_s = ld_l2(p.S[(t - 1) & 1] + c0);
                 c_v = ld_l2(p.W[(t - 1) & 1] + c0);
             }
+            // stamps are unique within the solve (mark is cleared at set-up)
+            const uint64_t stamp = p.mark ? (uint64_t)(k - p.start_sweep) * (uint64_t)p.T + (uint64_t)t + 1u : 0u;
             if (!batch<KIND>(A, B, t * p.b, len, ordered ? &K : nullptr, ordered ? p.S[t & 1] : nullptr,
                              ordered ? p.W[t & 1] : nullptr, acc))
                 return false;
-            if (c_s >= 0) st_l2(B + c_s, c_v);
-            if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B, gthreads());
+            uint64_t* mk = p.mark ? p.mark + (size_t)(t & 1) * (size_t)p.n : nullptr;
+            if (c_s >= 0 && !(stamp && ld_l2(mk + c_s) == stamp)) st_l2(B + c_s, c_v);
+            if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B, gthreads(), stamp, mk);
+            if (p.mark && t + 1 < p.T)
+                mark_batch(K, (t + 1) * p.b, (t + 2 == p.T) ? p.last_len : p.b, stamp + 1u,
+                           p.mark + (size_t)((t + 1) & 1) * (size_t)p.n);
             if (t == p.T - 1) publish(c, slot, acc, rs);
             arrive();
             if (t + 1 < p.T) prefetch_next<KIND>((t + 1) * p.b, (t + 2 == p.T) ? p.last_len : p.b, &K);
@@ -1243,7 +1278,9 @@ struct Runner {
             return false;
         }
         cur = newcur;
-        if (stop) return true;
+        // a solve that ends here skips the closing phase; with draws the caller may still go on
+        // (its full-residual check can fail), so the buffers and the next order must be completed
+        if (stop && (p.select == RMB_SELECT_PERMUTATION || is_last)) return true;
         const float shift = shift_for(lo, hi);
         if (shift != 0.f) {
             float* F = p.d[cur];
@@ -1256,7 +1293,8 @@ struct Runner {
             C = make_centre(C.mu + (double)shift, p.gamma_d);
             compute_perm(k + 1);
             if (!sync(20)) return false;
-        } else if (p.T >= 2 && !async) {
+        } else if ((p.T >= 2 || p.select != RMB_SELECT_PERMUTATION) && !async) {
+            // (one batch of draws leaves the states not drawn to be carried over as well)
             copy_batch(p.S[(p.T - 1) & 1], p.W[(p.T - 1) & 1], p.last_len, p.d[cur ^ 1]);
             compute_perm(k + 1);
             if (!sync(21)) return false;
@@ -1322,6 +1360,10 @@ struct Runner {
         __syncthreads();
         if (ld_volatile(&c->error) != 0) return;   // the validation pass rejected the MDP
 
+        if (p.select == RMB_SELECT_WEIGHTED) {
+            wtot = __ldg(p.cdf + (p.n - 1));
+            if (wtot == 0 && lead) atomicCAS(&c->error, 0, RMB_ERR_ARG);
+        }
         // set-up: centre on the midpoint of the start values
         Acc a0 = {0.f, kInf, -kInf};
         for (size_t i = gtid(); i < (size_t)p.n; i += gthreads()) {
@@ -1332,6 +1374,7 @@ struct Runner {
         }
         publish(c, 3, a0, rs);
         if (!sync(1)) return finish(false, 0, 0, 0.0);
+        if (ld_volatile(&c->error) != 0) return finish(false, 0, 0, 0.0);   // e.g. all weights zero
         float dm, lo, hi;
         read_slot(c, 3, rs, dm, lo, hi);
         // rows that need not sum to 1 (RMB_FLAG_RAW_ROWS) keep the values uncentred: mu = 0
@@ -1341,6 +1384,10 @@ struct Runner {
             const float v = (float)((double)p.Vin[i] - mu0);
             st_l2(p.d[0] + i, v);
             st_l2(p.d[1] + i, v);
+            if (p.mark) {
+                st_l2(p.mark + i, (uint64_t)0);
+                st_l2(p.mark + p.n + i, (uint64_t)0);
+            }
         }
         if (p.mode == MODE_VI || p.mode == MODE_EVAL) compute_perm(p.start_sweep);
         if (!sync(2)) return finish(false, 0, 0, 0.0);
@@ -1367,6 +1414,15 @@ struct Runner {
                 residual = (double)delta;
                 if (stop) {
                     converged = (double)delta <= p.eps;
+                    if (converged && p.select != RMB_SELECT_PERMUTATION) {
+                        // draws: the change covers only the drawn states; confirm with a full pass
+                        float r;
+                        if (!greedy_pass(r)) return finish(false, sweeps, 0, residual);   // also writes V
+                        residual = (double)r;
+                        converged = (double)r <= p.eps;
+                        if (converged) return finish(true, sweeps, 0, residual, true);
+                        if (!last) continue;
+                    }
                     break;
                 }
             }
@@ -1624,6 +1680,83 @@ __global__ void rmb_grad_kernel(int n, int m, int k, float gamma, const int32_t*
 // Gather-rate probe: every thread streams 16-byte chunks of an index array and gathers src at those
 // indices (L1-cached, as the successor gathers), accumulating a checksum per thread.  Measures the
 // attainable rate of random 4-byte gathers from a table of a given size (the CSR kernel's L2 bound).
+// ------------------------------------------------------------------------------------------------
+// Cumulative weights of RMB_SELECT_WEIGHTED (exact: 64-bit integer sums), in three launches:
+// per-tile sums, an exclusive scan of the tile sums by one CTA, then every tile's running sums.
+// ------------------------------------------------------------------------------------------------
+__device__ uint64_t block_exscan_u64(uint64_t v, uint64_t* total)
+{
+    __shared__ uint64_t warp_tot[kScanThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint64_t t = lane < nw ? warp_tot[lane] : 0;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t += y;
+        }
+        if (lane < nw) warp_tot[lane] = t;   // inclusive over warps
+    }
+    __syncthreads();
+    const uint64_t ex = (w > 0 ? warp_tot[w - 1] : 0) + x - v;
+    *total = warp_tot[nw - 1];
+    __syncthreads();                          // warp_tot is reused by the next call
+    return ex;
+}
+
+__global__ void __launch_bounds__(kScanThreads) rmb_wsum_kernel(const uint32_t* __restrict__ w, int64_t n,
+                                                               uint64_t* __restrict__ parts)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    uint64_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i)
+        if (base + i < n) sum += w[base + i];
+    uint64_t tot;
+    block_exscan_u64(sum, &tot);
+    if (threadIdx.x == 0) parts[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) rmb_wparts_kernel(uint64_t* __restrict__ parts, int64_t tiles)
+{
+    uint64_t carry = 0;
+    for (int64_t c0 = 0; c0 < tiles; c0 += kScanThreads) {
+        const int64_t i = c0 + threadIdx.x;
+        const uint64_t v = i < tiles ? parts[i] : 0;
+        uint64_t tot;
+        const uint64_t ex = block_exscan_u64(v, &tot);
+        if (i < tiles) parts[i] = carry + ex;
+        carry += tot;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) rmb_wcdf_kernel(const uint32_t* __restrict__ w, int64_t n,
+                                                               const uint64_t* __restrict__ parts,
+                                                               uint64_t* __restrict__ cdf)
+{
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+    uint64_t v[kScanPer];
+    uint64_t sum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        v[i] = base + i < n ? w[base + i] : 0;
+        sum += v[i];
+    }
+    uint64_t tot;
+    uint64_t run = parts[blockIdx.x] + block_exscan_u64(sum, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        run += v[i];
+        if (base + i < n) cdf[base + i] = run;
+    }
+}
+
 __global__ void __launch_bounds__(512, 1) rmb_gather_probe_kernel(const float* __restrict__ src, uint32_t nm1,
                                                                   const int4* __restrict__ idx, int64_t n4, int reps,
                                                                   float* __restrict__ out)
@@ -1787,9 +1920,10 @@ int dev_info(DevInfo** out)
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Layout {
-    size_t ctrl, d0, d1, s0, s1, w0, w1, pb, total;
+    size_t ctrl, d0, d1, s0, s1, w0, w1, pb, mark, cdf, parts, total;
     bool perm_buf;
 };
+
 
 // A sweep with at least this many batches precomputes its permutation into the workspace ...
 constexpr int64_t kPermBufMinBatches = 16;
@@ -1804,7 +1938,7 @@ bool use_perm_buf(int64_t n, int64_t b)
     return T >= kPermBufMinBatches || (T >= 2 && n < T * kPermBufPerBatch);
 }
 
-Layout layout(int64_t n, int64_t b)
+Layout layout(int64_t n, int64_t b, int select = RMB_SELECT_PERMUTATION)
 {
     Layout L;
     const size_t nb = align_up((size_t)n * 4, 256);
@@ -1818,7 +1952,12 @@ Layout layout(int64_t n, int64_t b)
     L.w1 = L.w0 + bb;
     L.pb = L.w1 + bb;
     L.perm_buf = use_perm_buf(n, b);
-    L.total = L.pb + (L.perm_buf ? nb : 0);
+    L.mark = L.pb + (L.perm_buf ? nb : 0);
+    const bool draws = select == RMB_SELECT_UNIFORM || select == RMB_SELECT_WEIGHTED;
+    L.cdf = L.mark + (draws && b < n ? align_up((size_t)n * 16, 256) : 0);
+    const bool w = select == RMB_SELECT_WEIGHTED;
+    L.parts = L.cdf + (w ? align_up((size_t)n * 8, 256) : 0);
+    L.total = L.parts + (w ? align_up((size_t)((n + kScanTile - 1) / kScanTile) * 8, 256) : 0);
     return L;
 }
 
@@ -1966,6 +2105,9 @@ int fill_kp(int mode, const rmb_mdp* M, const rmb_opts* O, int64_t b, char* ws, 
     // asynchronous sweeps have no barrier before a sweep's first read, so sigma is computed on the fly
     const bool async = (O->flags & RMB_FLAG_ASYNC) != 0;
     p.perm_buf = (L.perm_buf && mode != MODE_GREEDY && !async) ? reinterpret_cast<int32_t*>(ws + L.pb) : nullptr;
+    p.select = RMB_SELECT_PERMUTATION;   // solve() sets the selection rule of a single-MDP call
+    p.cdf = nullptr;
+    p.mark = nullptr;
     p.ctrl = ctrl;
     p.trace = mode == MODE_GREEDY ? nullptr : O->trace;
     p.timeout_ns = O->barrier_timeout_ns > 0 ? O->barrier_timeout_ns : 2000000000LL;
@@ -2020,7 +2162,12 @@ int solve(const Call& q)
     if (!q.Vin) return RMB_ERR_ARG;
     if (O->grid_ctas < 0 || O->barrier_timeout_ns < 0) return RMB_ERR_ARG;
     if ((O->flags & RMB_FLAG_ASYNC) && M->format != RMB_CSR) return RMB_ERR_UNSUPPORTED;
-    const Layout L = layout(M->n, b);
+    // batch selection (rmb_greedy has no order and ignores it)
+    const int select = q.mode == MODE_GREEDY ? RMB_SELECT_PERMUTATION : O->select;
+    if (select < RMB_SELECT_PERMUTATION || select > RMB_SELECT_WEIGHTED) return RMB_ERR_ARG;
+    if (select == RMB_SELECT_WEIGHTED && !O->weights) return RMB_ERR_ARG;
+    if (select != RMB_SELECT_PERMUTATION && q.mode == MODE_EVAL) return RMB_ERR_UNSUPPORTED;
+    const Layout L = layout(M->n, b, select);
     if (!q.ws || ((uintptr_t)q.ws & 255)) return RMB_ERR_WORKSPACE;
     if (q.ws_bytes < L.total) return RMB_ERR_WORKSPACE;
 
@@ -2030,6 +2177,10 @@ int solve(const Call& q)
     char* ws = static_cast<char*>(q.ws);
     KP p;
     int path = fill_kp(q.mode, M, O, b, ws, L, reinterpret_cast<Ctrl*>(ws + L.ctrl), p);
+    p.select = select;
+    p.cdf = select == RMB_SELECT_WEIGHTED ? reinterpret_cast<const uint64_t*>(ws + L.cdf) : nullptr;
+    // consecutive batches may share states only with draws, and only an asynchronous sweep has no copies
+    p.mark = (L.cdf > L.mark && !(O->flags & RMB_FLAG_ASYNC)) ? reinterpret_cast<uint64_t*>(ws + L.mark) : nullptr;
     p.Vin = q.Vin;
     p.Vout = q.Vout;
     p.TVout = q.TV;
@@ -2106,6 +2257,16 @@ int solve(const Call& q)
     }
     if (cudaMemsetAsync(p.ctrl, 0, sizeof(Ctrl), s) != cudaSuccess) return RMB_ERR_CUDA;
     if (O->validate && (st = launch_validate(M, &p.ctrl->error, s, D->sms))) return st;
+    if (select == RMB_SELECT_WEIGHTED) {
+        const int64_t tiles = (M->n + kScanTile - 1) / kScanTile;
+        uint64_t* parts = reinterpret_cast<uint64_t*>(ws + L.parts);
+        uint64_t* cdf = reinterpret_cast<uint64_t*>(ws + L.cdf);
+        rmb_wsum_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(O->weights, M->n, parts);
+        rmb_wparts_kernel<<<1, kScanThreads, 0, s>>>(parts, tiles);
+        rmb_wcdf_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(O->weights, M->n, parts, cdf);
+        g_launches += 3;
+        if (cudaGetLastError() != cudaSuccess) return RMB_ERR_CUDA;
+    }
     void* args[] = {&p};
     cudaError_t ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, s);
     g_launches++;
@@ -2364,7 +2525,7 @@ int check_batch(const rmb_batch_item* items, int count, const rmb_opts* O)
 {
     if (!items || count < 1 || !O) return RMB_ERR_ARG;
     if (O->max_sweeps < 1 || !(O->eps >= 0.0) || std::isinf(O->eps) || O->start_sweep < 0) return RMB_ERR_ARG;
-    if (O->flags & RMB_FLAG_ASYNC) return RMB_ERR_UNSUPPORTED;
+    if ((O->flags & RMB_FLAG_ASYNC) || O->select != RMB_SELECT_PERMUTATION) return RMB_ERR_UNSUPPORTED;
     for (int i = 0; i < count; ++i) {
         const int st = check_mdp(&items[i].mdp);
         if (st) return st;
@@ -2550,7 +2711,7 @@ size_t rmb_workspace_bytes(const rmb_mdp* mdp, const rmb_opts* opts)
     if (check_mdp(mdp)) return 0;
     int64_t b = mdp->n;
     if (opts && opts->batch >= 1) b = opts->batch > mdp->n ? mdp->n : opts->batch;
-    return layout(mdp->n, b).total;
+    return layout(mdp->n, b, opts ? opts->select : RMB_SELECT_PERMUTATION).total;
 }
 
 int rmb_vi(const rmb_mdp* mdp, const rmb_opts* opts, float* V_inout, int32_t* pi_out, float* qgap_out,
@@ -2649,6 +2810,7 @@ int rmb_fixed_point_grad(const rmb_mdp* mdp, const int32_t* pi, const float* V, 
     if (mdp->n * (int64_t)mdp->k_uniform >= ((int64_t)1 << 31)) return RMB_ERR_UNSUPPORTED;
     if (!pi || !V || !w || !lambda_out || !opts) return RMB_ERR_ARG;
     if (opts->batch < 1 || opts->max_sweeps < 1 || !(opts->eps >= 0.0) || std::isinf(opts->eps)) return RMB_ERR_ARG;
+    if (opts->select != RMB_SELECT_PERMUTATION) return RMB_ERR_UNSUPPORTED;
     const int64_t n = mdp->n;
     const int k = mdp->k_uniform;
     const int64_t b = opts->batch > n ? n : opts->batch;

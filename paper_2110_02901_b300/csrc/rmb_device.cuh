@@ -11,10 +11,10 @@ constexpr float kInf = __builtin_huge_valf();
 
 // ------------------------------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the multiply-xor round with the
-// key bumped by the Weyl increments between rounds.  Only the first output word is used here.
+// key bumped by the Weyl increments between rounds.  The first two output words are used.
 // ------------------------------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                              uint32_t k0, uint32_t k1)
+__device__ __forceinline__ uint2 philox_x01(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
@@ -27,7 +27,13 @@ __device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    return c0;
+    return make_uint2(c0, c1);
+}
+
+__device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1)
+{
+    return philox_x01(c0, c1, c2, c3, k0, k1).x;
 }
 
 // Processing order of one sweep (Sec. III-A): sigma(p) by an 8-round balanced Feistel network on
@@ -36,7 +42,10 @@ __device__ __forceinline__ uint32_t philox_x0(uint32_t c0, uint32_t c1, uint32_t
 // to [0,n) within (4^h - n + 1) steps; *ok is cleared if that bound is ever exceeded.
 struct PermKey {
     uint32_t n, h, mask, k0, k1, s_lo, s_hi;
-    const int32_t* buf;   // non-null: sigma of this sweep is precomputed here (buf[p] = sigma(p))
+    const int32_t* buf;   // non-null: the order of this sweep is precomputed here (buf[p] = state)
+    uint32_t select;      // 0: sigma; 1: uniform draws; 2: draws by weight (with replacement)
+    uint64_t wtot;        // select 2: sum of the weights
+    const uint64_t* cdf;  // select 2: cdf[s] = w_0 + ... + w_s
 };
 
 __device__ __forceinline__ uint32_t feistel8(uint32_t x, const PermKey& K)
@@ -64,11 +73,37 @@ __device__ __forceinline__ uint32_t perm_at(uint32_t p, const PermKey& K, bool* 
     return x;
 }
 
-// sigma(p) from the precomputed buffer when there is one, else evaluated here
+// Batch selection with replacement (the Sec. V extension): u = x0 * 2^32 + x1 of
+// Philox(ctr = {p, 2^31, sweep_lo, sweep_hi}, key = seed) -- a counter word the Feistel rounds
+// (0..7) never use -- then floor(u n / 2^64) (uniform), or r = floor(u W / 2^64) and the first s
+// with cdf[s] > r (by weight), all in integers.
+__device__ __forceinline__ int draw_at(uint32_t p, const PermKey& K)
+{
+    const uint2 x = philox_x01(p, 0x80000000u, K.s_lo, K.s_hi, K.k0, K.k1);
+    const uint64_t u = ((uint64_t)x.x << 32) | x.y;
+    if (K.select == 1) return (int)__umul64hi(u, (uint64_t)K.n);
+    const uint64_t r = __umul64hi(u, K.wtot);
+    uint32_t lo = 0, hi = K.n - 1;
+    while (lo < hi) {   // at most ceil(log2 n) steps: the interval halves every time
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(K.cdf + mid) > r) hi = mid;
+        else lo = mid + 1;
+    }
+    return (int)lo;
+}
+
+// the state at position p of the sweep's order, evaluated here (no buffer)
+__device__ __forceinline__ int order_at(uint32_t p, const PermKey& K, bool* ok)
+{
+    if (K.select) return draw_at(p, K);
+    return (int)perm_at(p, K, ok);
+}
+
+// the state at position p: from the precomputed buffer when there is one, else evaluated here
 __device__ __forceinline__ int state_at(uint32_t p, const PermKey& K, bool* ok)
 {
     if (K.buf) return __ldcg(K.buf + p);
-    return (int)perm_at(p, K, ok);
+    return order_at(p, K, ok);
 }
 
 __host__ __device__ inline uint32_t perm_half_bits(int64_t n)
@@ -87,6 +122,14 @@ __device__ __forceinline__ float ld_l2(const float* p) { return __ldcg(p); }
 __device__ __forceinline__ int ld_l2(const int* p) { return __ldcg(p); }
 __device__ __forceinline__ void st_l2(float* p, float v) { __stcg(p, v); }
 __device__ __forceinline__ void st_l2(int* p, int v) { __stcg(p, v); }
+__device__ __forceinline__ uint64_t ld_l2(const uint64_t* p)
+{
+    return __ldcg(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ void st_l2(uint64_t* p, uint64_t v)
+{
+    __stcg(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
 
 __device__ __forceinline__ int ld_volatile(const int* p)
 {

@@ -49,10 +49,11 @@ def test_struct_layouts_match_header():
 #include <stddef.h>
 #include "rmb.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rmb_mdp), sizeof(rmb_opts), sizeof(rmb_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(rmb_mdp), sizeof(rmb_opts), sizeof(rmb_stats),
          offsetof(rmb_mdp, gamma), offsetof(rmb_mdp, k_uniform), offsetof(rmb_opts, trace),
          offsetof(rmb_stats, ms), offsetof(rmb_opts, flags), offsetof(rmb_mdp, row_scale),
-         sizeof(rmb_batch_item), sizeof(rmb_batch_handle), sizeof(rmb_batch_plan_item));
+         sizeof(rmb_batch_item), sizeof(rmb_batch_handle), sizeof(rmb_batch_plan_item),
+         offsetof(rmb_opts, select), offsetof(rmb_opts, weights));
   return 0;
 }'''
     d = tempfile.mkdtemp()
@@ -65,7 +66,7 @@ int main(void) {
             rmb.rmb_mdp.gamma.offset, rmb.rmb_mdp.k_uniform.offset, rmb.rmb_opts.trace.offset,
             rmb.rmb_stats.ms.offset, rmb.rmb_opts.flags.offset, rmb.rmb_mdp.row_scale.offset,
             ctypes.sizeof(rmb.rmb_batch_item), ctypes.sizeof(rmb.rmb_batch_handle),
-            ctypes.sizeof(rmb.rmb_batch_plan_item)]
+            ctypes.sizeof(rmb.rmb_batch_plan_item), rmb.rmb_opts.select.offset, rmb.rmb_opts.weights.offset]
     assert vals == mine
 
 
@@ -165,3 +166,26 @@ def test_workspace_size_formula(L):
     assert L.rmb_workspace_bytes(ctypes.byref(big), ctypes.byref(o)) == 256 + 2 * (4 << 20) + 4 * bb
     d.gamma = 2.0
     assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == 0
+
+
+def test_batch_selection_arguments(L):
+    d, o = _fake_mdp(), _opts()
+    o.select = 3
+    assert L.rmb_vi(ctypes.byref(d), ctypes.byref(o), 4096, None, None, 8192, 1 << 30, None, None) == rmb.RMB_ERR_ARG
+    o.select = rmb.RMB_SELECT_WEIGHTED       # weights missing
+    assert L.rmb_vi(ctypes.byref(d), ctypes.byref(o), 4096, None, None, 8192, 1 << 30, None, None) == rmb.RMB_ERR_ARG
+    o.select = rmb.RMB_SELECT_UNIFORM        # policy evaluation has no full-residual stop rule for draws
+    assert L.rmb_eval_policy(ctypes.byref(d), 4096, ctypes.byref(o), 4096, 8192, 1 << 30, None, None) == \
+        rmb.RMB_ERR_UNSUPPORTED
+    # draws add 16 bytes per state of batch marks when b < n; weights another 8 per state of
+    # cumulative weights (+ 8 per 8192 states of tile sums)
+    o.select = rmb.RMB_SELECT_PERMUTATION
+    base = L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o))
+    o.select = rmb.RMB_SELECT_WEIGHTED
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == base + 1792 + 1024 + 256
+    o.select = rmb.RMB_SELECT_UNIFORM
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == base + 1792
+    o.batch = 100           # b = n: one batch, no marks
+    base = L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o))
+    o.select = rmb.RMB_SELECT_PERMUTATION
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == base
