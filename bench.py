@@ -221,7 +221,8 @@ def main():
     ap.add_argument("--n-log2", type=int, default=20, help="states = 2^n_log2 (profiling of smaller cases)")
     ap.add_argument("--profile-case", type=int, default=0, metavar="SWEEPS",
                     help="profiling mode: one MB-VI solve of exactly SWEEPS sweeps (no bench line)")
-    ap.add_argument("--workload", default="csr", choices=["csr", "dense500", "dense16k", "batched", "adjoint", "maze"],
+    ap.add_argument("--workload", default="csr",
+                    choices=["csr", "dense500", "dense16k", "batched", "adjoint", "maze", "select"],
                     help="csr: the headline line (default); the others measure the remaining workloads")
     ap.add_argument("--full", action="store_true", help="dense16k: also time full gamma=0.999 solves at n=16384")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"],
@@ -435,7 +436,7 @@ def run_workload(args, world, rank, local):
     l0 = rmb.rmb_kernel_launches()
     with ClockSampler(local) as clk:
         line = {"dense500": _dense500, "dense16k": _dense16k, "batched": _batched, "adjoint": _adjoint,
-                "maze": _maze}[
+                "maze": _maze, "select": _select}[
             args.workload](args, world, rmb, torch, stream, hbm, peak_kind)
     line["clocks"] = clk.summary()
     line["gpu_launches_total"] = rmb.rmb_kernel_launches() - l0
@@ -740,6 +741,112 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
                  roofline=None,
                  cpu_baseline={"value": 1.0 / ct, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
                                "sample": f"N=100 maze, b=512, {k512} sweeps, {ct:.2f} s"})
+
+
+def _select(args, world, rmb, torch, stream, hbm, peak_kind):
+    """Batch selection (the Sec. V extension): sigma (the paper's order) against uniform draws with
+    replacement and draws by residual weights (refreshed every few sweeps).
+    (1) CSR n = 2^20, m = 8, k = 32, gamma = 0.99, from V = 0 to 1e-6: time, sweeps and the full
+        residual ||TV - V||_inf at the end (draws stop on it; sigma stops on the sweep change);
+    (2) warm start on the N = 100 maze after the costs of a 10 x 10 block of cells rise from 1 to 3:
+        time from the old J* to ||V - J*_new||_inf <= 1e-4 (k* found by stepping, as for the maze workload)."""
+    rows = []
+    mdp = mdpgen.config2()
+    dm = rmb.DeviceMDP.from_host(mdp)
+    n = mdp.n
+    V = torch.zeros(n, dtype=torch.float32, device="cuda")
+    TV = torch.empty_like(V)
+    gws = rmb.workspace(dm, rmb.Opts(batch=n))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for b in (16384, 262144):
+        for label in ("sigma", "uniform", "prioritized"):
+            ts, st = [], None
+            for _ in range(2):
+                V.zero_()
+                torch.cuda.synchronize()
+                ev0.record(stream)
+                if label == "prioritized":
+                    st = rmb.prioritized_vi(dm, V, batch=b, eps=EPS, refresh=16, floor_frac=0.05, stream=stream)
+                else:
+                    st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=200000,
+                                                 validate=False, select=0 if label == "sigma" else 1), V, stream=stream)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(ev0.elapsed_time(ev1))
+            full = rmb.rmb_greedy(dm, V, TV, ws=gws)["residual"]
+            rows.append({"mdp": "csr2e20", "b": b, "selection": label, "ms": round(min(ts), 2), "sweeps": st["sweeps"],
+                         "ms_per_sweep": round(min(ts) / st["sweeps"], 4), "full_residual": full,
+                         "status": st["status"]})
+    # (2) maze warm start
+    old = mdpgen.maze100()
+    new = mdpgen.maze100()
+    cells = new.meta["cells"]
+    block = np.flatnonzero((cells[:, 0] >= 45) & (cells[:, 0] < 55) & (cells[:, 1] >= 45) & (cells[:, 1] < 55))
+    block = block[block != new.meta["goal"]]
+    cost = new.cost.reshape(new.n, 4).copy()
+    cost[block] = 3.0
+    new.cost = cost.reshape(-1).astype(np.float32)
+    dold, dnew = rmb.DeviceMDP.from_host(old), rmb.DeviceMDP.from_host(new)
+    n = new.n
+    J0 = torch.zeros(n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(n, dtype=torch.int32, device="cuda")
+    rmb.rmb_mpi(dold, rmb.Opts(batch=n, eps=1e-7, max_sweeps=100000, eval_sweeps=50), J0, pi)
+    J1 = J0.clone()
+    rmb.rmb_mpi(dnew, rmb.Opts(batch=n, eps=1e-7, max_sweeps=100000, eval_sweeps=50), J1, pi)
+    V = torch.empty_like(J0)
+    TOL = 1e-4
+
+    def err():
+        return float((V - J1).abs().max())
+
+    init_err = float((J0 - J1).abs().max())
+    for label, b, refresh in (("sigma", n, 0), ("sigma", 512, 0), ("uniform", 512, 0), ("prioritized", 512, 1),
+                              ("prioritized", 512, 4), ("prioritized", 2048, 4)):
+        def run(cap):
+            if label == "prioritized":
+                done = 0
+                while done < cap:
+                    w = rmb.rmb_residual_weights(dnew, V, 0.05, stream=stream)
+                    k = min(refresh, cap - done)
+                    rmb.rmb_vi(dnew, rmb.Opts(batch=b, seed=7, eps=0.0, max_sweeps=k, start_sweep=done, validate=False,
+                                              select=2, weights=w), V, stream=stream, stats=False)
+                    done += k
+            else:
+                rmb.rmb_vi(dnew, rmb.Opts(batch=b, seed=7, eps=0.0, max_sweeps=cap, validate=False,
+                                          select=0 if label == "sigma" else 1), V, stream=stream, stats=False)
+        # k*: smallest sweep count reaching TOL (doubling, then bisection; each trial from the old J*)
+        lo, hi = 0, 1
+        while True:
+            V.copy_(J0)
+            run(hi)
+            torch.cuda.synchronize()
+            if err() <= TOL or hi > 4096:
+                break
+            lo, hi = hi, hi * 2
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            V.copy_(J0)
+            run(mid)
+            torch.cuda.synchronize()
+            lo, hi = (lo, mid) if err() <= TOL else (mid, hi)
+        ts = []
+        for _ in range(3):
+            V.copy_(J0)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            run(hi)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev0.elapsed_time(ev1))
+        rows.append({"mdp": "maze100 warm start", "b": b, "selection": label + (f" refresh={refresh}" if refresh else ""),
+                     "ms": round(min(ts), 3), "sweeps": hi, "err": err()})
+    best = next(r for r in rows if r["mdp"] == "csr2e20" and r["b"] == 262144 and r["selection"] == "uniform")
+    return _line("batch selection with replacement: CSR n=2^20 MB-VI to 1e-6 with uniform draws (b=262144)",
+                 mdp.n * best["sweeps"] / (best["ms"] / 1e3), "Bellman backups/s", best["ms"], args, world,
+                 {"workload": "csr-mdp n=2^20 m=8 k=32 gamma=0.99 (sigma / uniform draws / residual-weighted draws, "
+                              "b in {16384, 262144}); maze N=100 warm start after a 10x10 cost block rises 1 -> 3",
+                  "table": rows, "maze_initial_err": init_err, "maze_block_states": int(len(block))},
+                 roofline=None, cpu_baseline=None)
 
 
 if __name__ == "__main__":

@@ -251,6 +251,21 @@ int rmb_vi_noalloc(const rmb_mdp *mdp, const rmb_opts *opts, float *V_inout, int
                    float *qgap_out, rmb_stats *stats, void *stream);
 
 /*
+ * Importance weights for RMB_SELECT_WEIGHTED from the Bellman residual (Sec. V suggests importance
+ * sampling and epsilon-greedy selection of the batch states; the rule is the library's): one
+ * Bellman pass at V gives r(s) = |TV(s) - V(s)| (float32, from TV and V as floats) and R = max r;
+ *   weights_out[s] = floor(2^20 * (floor_frac + (1 - floor_frac) * r(s) / R))   (2^20 if R = 0),
+ * so every state keeps probability >= floor_frac / (2^20 n) of the total when floor_frac > 0 (the
+ * epsilon-greedy part) and the rest goes in proportion to the residual.
+ *   V [n] float32, weights_out [n] uint32, device; floor_frac in [0, 1].
+ *   workspace: rmb_residual_weights_workspace_bytes(mdp) bytes, 256-byte aligned.
+ * Asynchronous on `stream`; argument errors return before any launch.  MDPs as for rmb_greedy.
+ */
+size_t rmb_residual_weights_workspace_bytes(const rmb_mdp *mdp);
+int rmb_residual_weights(const rmb_mdp *mdp, const float *V, float floor_frac, uint32_t *weights_out,
+                         void *workspace, size_t workspace_bytes, void *stream);
+
+/*
  * P(.|s,a) = softmax of the row's logits over its k successors (RMB_CSR with k_uniform = k > 0):
  * the parametrisation whose gradient rmb_fixed_point_grad returns.  logits, prob_out: [n*m*k], device.
  */

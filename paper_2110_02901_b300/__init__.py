@@ -289,6 +289,46 @@ def rmb_eval_policy(mdp: DeviceMDP, pi, opts: Opts, V, ws=None, stats: bool = Tr
     return _finish(st, s, "rmb_eval_policy") if check else (st, s.as_dict() if s is not None else None)
 
 
+def rmb_residual_weights(mdp: DeviceMDP, V, floor_frac: float = 0.05, out=None, ws=None, stream=None):
+    """Importance weights (uint32 in an int32 tensor [n]) from the Bellman residual at V (see rmb.h)."""
+    import torch
+    _check(V, torch.float32, mdp.n, "V")
+    L = lib()
+    L.rmb_residual_weights_workspace_bytes.argtypes = [ctypes.POINTER(rmb_mdp)]
+    L.rmb_residual_weights_workspace_bytes.restype = ctypes.c_size_t
+    L.rmb_residual_weights.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    L.rmb_residual_weights.restype = ctypes.c_int
+    if ws is None:
+        nb = int(L.rmb_residual_weights_workspace_bytes(ctypes.byref(mdp.desc)))
+        if nb == 0:
+            raise RmbError(RMB_ERR_ARG, "rmb_residual_weights_workspace_bytes")
+        ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    out = torch.empty(mdp.n, dtype=torch.int32, device="cuda") if out is None else out
+    _check(out, torch.int32, mdp.n, "weights")
+    st = L.rmb_residual_weights(ctypes.byref(mdp.desc), _ptr(V), float(floor_frac), _ptr(out), _ptr(ws), ws.numel(),
+                                _stream_handle(stream))
+    if st != RMB_OK:
+        raise RmbError(st, "rmb_residual_weights")
+    return out
+
+
+def prioritized_vi(mdp: DeviceMDP, V, batch: int, eps: float, refresh: int = 4, floor_frac: float = 0.05,
+                   seed: int = 12345, max_rounds: int = 100000, pi=None, stream=None):
+    """MB-VI whose batches are drawn by residual weights, refreshed every `refresh` sweeps (the
+    importance-sampled selection suggested in Sec. V); stops when ||TV - V||_inf <= eps.
+    Returns dict(sweeps, rounds, residual, status)."""
+    sweeps = 0
+    for r in range(max_rounds):
+        w = rmb_residual_weights(mdp, V, floor_frac, stream=stream)
+        st = rmb_vi(mdp, Opts(batch=batch, seed=seed, eps=eps, max_sweeps=refresh, start_sweep=sweeps,
+                              validate=False, select=RMB_SELECT_WEIGHTED, weights=w), V, pi, stream=stream)
+        sweeps += st["sweeps"]
+        if st["status"] == RMB_OK:
+            return {"sweeps": sweeps, "rounds": r + 1, "residual": st["residual"], "status": RMB_OK}
+    return {"sweeps": sweeps, "rounds": max_rounds, "residual": st["residual"], "status": RMB_ERR_NOT_CONVERGED}
+
+
 def rmb_greedy(mdp: DeviceMDP, V, TV=None, pi=None, qgap=None, opts: Optional[Opts] = None, ws=None,
                stats: bool = True, stream=None, check: bool = True):
     """One Bellman pass at V: TV, greedy policy, Q-gap; stats['residual'] = ||TV - V||_inf."""

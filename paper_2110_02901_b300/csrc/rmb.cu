@@ -1757,6 +1757,32 @@ __global__ void __launch_bounds__(kScanThreads) rmb_wcdf_kernel(const uint32_t* 
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Importance weights from the Bellman residual: r(s) = |TV(s) - V(s)|, R = max r, then
+// w(s) = floor(2^20 (f + (1 - f) r(s) / R)).
+// ------------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) rmb_resid_max_kernel(const float* __restrict__ TV, const float* __restrict__ V,
+                                                            int64_t n, uint32_t* __restrict__ rmax)
+{
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(TV[i] - V[i]));
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(rmax, __float_as_uint(m));   // non-negative floats order as their bits
+}
+
+__global__ void __launch_bounds__(256) rmb_resid_weights_kernel(const float* __restrict__ TV,
+                                                                const float* __restrict__ V, int64_t n, float f,
+                                                                const uint32_t* __restrict__ rmax,
+                                                                uint32_t* __restrict__ w)
+{
+    const float R = __uint_as_float(*rmax);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = R > 0.f ? fminf(fabsf(TV[i] - V[i]) / R, 1.f) : 1.f;
+        w[i] = (uint32_t)floorf(1048576.f * (f + (1.f - f) * x));
+    }
+}
+
 __global__ void __launch_bounds__(512, 1) rmb_gather_probe_kernel(const float* __restrict__ src, uint32_t nm1,
                                                                   const int4* __restrict__ idx, int64_t n4, int reps,
                                                                   float* __restrict__ out)
@@ -2789,6 +2815,43 @@ int rmb_softmax_rows(const rmb_mdp* mdp, const float* logits, float* prob_out, v
     const int blocks = (int)std::min<int64_t>((rows + 7) / 8, (int64_t)D->sms * 16);
     rmb_softmax_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(rows, mdp->k_uniform, logits, prob_out);
     g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
+}
+
+size_t rmb_residual_weights_workspace_bytes(const rmb_mdp* mdp)
+{
+    if (check_mdp(mdp)) return 0;
+    // one Bellman pass (b = n) + TV [n] + the maximum
+    return layout(mdp->n, mdp->n).total + align_up((size_t)mdp->n * 4, 256) + 256;
+}
+
+int rmb_residual_weights(const rmb_mdp* mdp, const float* V, float floor_frac, uint32_t* weights_out,
+                         void* workspace, size_t workspace_bytes, void* stream)
+{
+    int st = check_mdp(mdp);
+    if (st) return st;
+    if (!V || !weights_out || !(floor_frac >= 0.f && floor_frac <= 1.f)) return RMB_ERR_ARG;
+    const size_t need = rmb_residual_weights_workspace_bytes(mdp);
+    if (!workspace || ((uintptr_t)workspace & 255)) return RMB_ERR_WORKSPACE;
+    if (workspace_bytes < need) return RMB_ERR_WORKSPACE;
+    const size_t g = layout(mdp->n, mdp->n).total;
+    char* ws = static_cast<char*>(workspace);
+    float* TV = reinterpret_cast<float*>(ws + g);
+    uint32_t* rmax = reinterpret_cast<uint32_t*>(ws + g + align_up((size_t)mdp->n * 4, 256));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    rmb_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.batch = mdp->n;
+    o.max_sweeps = 1;
+    Call q{MODE_GREEDY, mdp, &o, V, nullptr, TV, nullptr, nullptr, nullptr, ws, g, nullptr, s};
+    if ((st = solve(q))) return st;
+    DevInfo* D = nullptr;
+    if ((st = dev_info(&D))) return st;
+    if (cudaMemsetAsync(rmax, 0, sizeof(uint32_t), s) != cudaSuccess) return RMB_ERR_CUDA;
+    const int grid = D->sms * 4;
+    rmb_resid_max_kernel<<<grid, 256, 0, s>>>(TV, V, mdp->n, rmax);
+    rmb_resid_weights_kernel<<<grid, 256, 0, s>>>(TV, V, mdp->n, floor_frac, rmax, weights_out);
+    g_launches += 2;
     return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
 }
 

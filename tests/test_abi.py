@@ -189,3 +189,19 @@ def test_batch_selection_arguments(L):
     base = L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o))
     o.select = rmb.RMB_SELECT_PERMUTATION
     assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) == base
+
+
+def test_residual_weights_arguments(L):
+    d = _fake_mdp(n=1000)
+    L.rmb_residual_weights_workspace_bytes.argtypes = [ctypes.POINTER(rmb.rmb_mdp)]
+    L.rmb_residual_weights_workspace_bytes.restype = ctypes.c_size_t
+    nb = L.rmb_residual_weights_workspace_bytes(ctypes.byref(d))
+    # a Bellman pass (b = n: control + 6 arrays of n floats) + TV + the maximum
+    assert nb == 256 + 6 * 4096 + 4096 + 256
+    f = L.rmb_residual_weights
+    f.argtypes = [ctypes.POINTER(rmb.rmb_mdp), ctypes.c_void_p, ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_size_t, ctypes.c_void_p]
+    for frac in (-0.1, 1.5, float("nan")):
+        assert f(ctypes.byref(d), 4096, frac, 8192, 1 << 20, nb, None) == rmb.RMB_ERR_ARG
+    assert f(ctypes.byref(d), None, 0.1, 8192, 1 << 20, nb, None) == rmb.RMB_ERR_ARG
+    assert f(ctypes.byref(d), 4096, 0.1, 8192, 1 << 20, nb - 1, None) == rmb.RMB_ERR_WORKSPACE

@@ -163,3 +163,30 @@ def test_refusals():
     # the solver still works afterwards
     st = rmb.rmb_vi(dm, rmb.Opts(batch=10, select=1, eps=1e-6), V)
     assert st["status"] == rmb.RMB_OK
+
+
+def test_residual_weights_match_the_oracles_residual():
+    mdp = mdpgen.csr_uniform_k(5000, 4, 16, gamma=0.95, seed=12)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    V0 = mdpgen.random_values(mdp.n, seed=3)
+    f = 0.05
+    w = rmb.rmb_residual_weights(dm, torch.from_numpy(V0).cuda(), f).cpu().numpy().view(np.uint32).astype(np.int64)
+    TV, _, _, _ = oracle.greedy(mdp, V0.astype(np.float64))
+    r = np.abs(TV - V0)
+    R = r.max()
+    want = np.floor(2.0 ** 20 * (f + (1 - f) * r / R))
+    # TV is rounded to float32 on the device: r moves by up to ~2 ulp of max(|TV|, |V|)
+    tol = 2.0 + 2.0 ** 20 * (1 - f) * 4 * np.finfo(np.float32).eps * max(np.abs(TV).max(), np.abs(V0).max()) / R
+    assert np.abs(w - want).max() <= tol
+    assert w.min() >= int(np.floor(2.0 ** 20 * f)) - 1 and w.max() <= 2 ** 20
+    assert r[np.argmax(w)] >= R * (1 - 1e-5)
+
+
+def test_prioritized_vi_reaches_the_optimum():
+    mdp = mdpgen.maze(40, 1500, gamma=0.95, slip=0.2, seed=9)
+    jstar, _, _ = exact.policy_iteration(mdp)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    res = rmb.prioritized_vi(dm, V, batch=64, eps=1e-6, refresh=4, floor_frac=0.05)
+    assert res["status"] == rmb.RMB_OK and res["residual"] <= 1e-6
+    close(V.cpu().numpy(), jstar)
