@@ -35,6 +35,7 @@ import mdpgen  # noqa: E402
 METRIC = "time-to-1e-6 residual and Bellman backups/s vs batch b; P-stream HBM GB/s"
 N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
+CSR_DRAM_BYTES_PER_STATE_PASS = 11180080896 / (21 * 262144)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]
 HEADLINE_B = 262144
 MPI_K = 10
@@ -299,8 +300,12 @@ def main():
     hbm, peak_kind = peaks()
     per_launch_bytes = [(s["sweeps"] + 1) * sweep_bytes(n, M_ACTIONS, K_SUCC) for s in stats]
     achieved = sum(per_launch_bytes) / (kernel_ms / 1e3) / 1e9
+    # DRAM bytes per state and pass from one ncu capture of this kernel (n = 2^18, b = 65536, 20 sweeps
+    # + the greedy pass: 11.180 GB); the values stay in L2, so traffic scales with states x passes
+    traffic = statistics.mean((s["sweeps"] + 1) * n * CSR_DRAM_BYTES_PER_STATE_PASS for s in stats)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "rmb_csr_vec_kernel", "peak_kind": peak_kind,
+                "traffic": traffic, "traffic_note": "ncu capture at n=2^18 scaled by states x passes",
+                "kernel": "rmb_csr_vec_kernel", "peak_kind": peak_kind,
                 "bytes_per_launch": statistics.mean(per_launch_bytes),
                 "note": "P stream (prob+col+cost) per sweep x (sweeps + 1 greedy pass) / launch time"}
 
