@@ -176,56 +176,15 @@ __device__ __forceinline__ Best csr_vec_state(const KP& p, int s, int pi_s, bool
     return best;
 }
 
-// Q-factors of one state on the generic CSR path (ragged rows).  The m rows of a state are
-// contiguous; when they hold at most 32 entries in all, lane e takes entry e of the state, a
-// segmented warp scan sums every row, and the row ends combine to the minimum (three dependent
-// loads per state).  With a policy (pi_s >= 0) only that row's lanes load, at the same lanes and
-// through the same scan, so T_pi and the Q-factor of the improvement pass round identically.
-// Otherwise the whole warp walks each row in turn.
+// Q-factors of one state on the generic CSR path, walking each row in turn with the whole warp
+// (states whose rows hold more than 32 entries, or m >= 32; the others take the one-pass form of
+// gen_eval below).
 template <bool ARG>
 __device__ __forceinline__ Best csr_gen_state(const KP& p, int s, int pi_s, bool act,
                                               const float* __restrict__ A, int lane)
 {
     const int nrows = pi_s >= 0 ? 1 : p.m;
     const uint32_t nm1 = (uint32_t)(p.n - 1);
-    if (p.m < 32) {
-        const int64_t r0 = (int64_t)s * p.m;
-        long long rp = 0;
-        float c = kInf;
-        if (act && lane <= p.m) rp = __ldg(p.row_ptr + r0 + lane);   // lane l < m: start of row l; lane m: end
-        if (act && lane < p.m) c = __ldg(p.cost + r0 + lane);
-        const long long E0 = __shfl_sync(0xffffffffu, rp, 0);
-        const long long E1 = __shfl_sync(0xffffffffu, rp, p.m);
-        if (E1 - E0 <= 32) {
-            const long long nxt = __shfl_down_sync(0xffffffffu, rp, 1);
-            const int len = lane < p.m ? (int)(nxt - rp) : 0;
-            uint32_t starts = (act && len > 0) ? (1u << (int)(rp - E0)) : 0u;   // heads of non-empty rows
-            for (int off = 16; off > 0; off >>= 1) starts |= __shfl_xor_sync(0xffffffffu, starts, off);
-            int lo = 0, hi = (int)(E1 - E0);
-            if (pi_s >= 0) {
-                lo = (int)(__shfl_sync(0xffffffffu, rp, pi_s) - E0);
-                hi = (int)(__shfl_sync(0xffffffffu, rp, pi_s + 1) - E0);
-            }
-            float x = 0.f;
-            if (act && lane >= lo && lane < hi) {
-                const long long e = E0 + lane;
-                x = __ldcs(p.prob + e) * gather(A, __ldcs(p.col + e), nm1);
-            }
-            // inclusive scan within rows: add the value d lanes down unless a row starts in between
-            for (int d = 1; d < 32; d <<= 1) {
-                const float y = __shfl_up_sync(0xffffffffu, x, d);
-                if (lane >= d && ((starts >> (lane - d + 1)) & ((1u << d) - 1u)) == 0u) x += y;
-            }
-            const float sum = __shfl_sync(0xffffffffu, x, len > 0 ? (int)(nxt - E0) - 1 : 0);
-            Best cur = {kInf, 0x7fffffff, kInf};
-            if (act && (pi_s >= 0 ? lane == pi_s : lane < p.m)) {
-                cur.a = lane;
-                cur.q = (c == kInf) ? kInf : fmaf(p.gamma, len > 0 ? sum : 0.f, c);
-            }
-            for (int off = 16; off > 0; off >>= 1) cur = better(cur, shfl_xor_best<ARG>(cur, off));
-            return cur;
-        }
-    }
     Best best = {kInf, 0x7fffffff, kInf};
     for (int ai = 0; ai < nrows; ++ai) {
         const int a = pi_s >= 0 ? pi_s : ai;
@@ -274,11 +233,22 @@ __device__ __forceinline__ float new_value(float q, const Centre& C) { return (q
 
 // Per-state epilogue shared by the CSR and dense paths.
 template <int KIND>
+__device__ __forceinline__ void state_epilogue_old(const KP& p, const Best& r, int s, int i, float old, float* B,
+                                                   int32_t* Sout, float* Wout, const Centre& C, Acc& acc);
+
+template <int KIND>
 __device__ __forceinline__ void state_epilogue(const KP& p, const Best& r, int s, int i, const float* A,
                                                float* B, int32_t* Sout, float* Wout, const Centre& C,
                                                Acc& acc)
 {
-    const float old = ld_l2(A + s);
+    state_epilogue_old<KIND>(p, r, s, i, ld_l2(A + s), B, Sout, Wout, C, acc);
+}
+
+// the same with the state's value before the batch already loaded
+template <int KIND>
+__device__ __forceinline__ void state_epilogue_old(const KP& p, const Best& r, int s, int i, float old, float* B,
+                                                   int32_t* Sout, float* Wout, const Centre& C, Acc& acc)
+{
     const float v = new_value(r.q, C);
     if (v != v) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
     if (KIND == K_GREEDY) {
@@ -334,6 +304,175 @@ __device__ void csr_batch(const KP& p, const GroupView& gv, int lps, const float
                                : csr_gen_state<ARG>(p, ss, pi_s, act, A, lane);
             if (act && lane_g == 0) state_epilogue<KIND>(p, r, s, first + g + j * U, A, B, Sout, Wout, C, acc);
         }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Generic CSR path (ragged rows), one warp per state, software-pipelined: while state j gathers its
+// successor values and reduces, the entries of state j+1 and the row pointers of state j+2 load.
+// The m rows of a state are contiguous; when they hold at most 32 entries in all (and m < 32), lane e
+// holds entry e of the state, a segmented warp scan sums every row and the row ends combine to the
+// minimum.  With a policy only that row's lanes load, at the same lanes and through the same scan,
+// so T_pi and the improvement pass's Q-factor round identically.
+// ------------------------------------------------------------------------------------------------
+struct GenRegs {
+    int s;          // state (-1: none); the same in every lane of the warp
+    int pi_s;       // K_POLICY: its action, else -1
+    long long rp;   // lane l <= m: start of row l (lane m: end of the last row)
+    float c;        // lane l < m: cost of row l
+    float pr;       // lane e: entry e of the state's rows (one-pass form)
+    int col;
+    bool has;       // this lane holds an entry
+    bool has_old;   // old holds the state's value before the batch (loaded with the rows)
+    float old;
+};
+
+// A: the batch's read buffer, or nullptr when its value may still change before the evaluation
+// (across a barrier, or in place in an asynchronous sweep): the epilogue then loads it
+template <int KIND>
+__device__ __forceinline__ void gen_stage1(const KP& p, int s, int lane, GenRegs& R, const float* A)
+{
+    R.s = s;
+    R.has_old = A != nullptr && s >= 0;
+    R.old = R.has_old && lane == 0 ? ld_l2(A + s) : 0.f;
+    R.pi_s = -1;
+    R.rp = 0;
+    R.c = kInf;
+    R.pr = 0.f;
+    R.col = 0;
+    R.has = false;
+    if (s < 0) return;
+    if (KIND == K_POLICY) R.pi_s = (int)min((uint32_t)ld_l2(p.pi_in ? p.pi_in + s : p.pi + s), (uint32_t)(p.m - 1));
+    if (p.m < 32) {
+        const int64_t r0 = (int64_t)s * p.m;
+        if (lane <= p.m) R.rp = __ldg(p.row_ptr + r0 + lane);
+        if (lane < p.m) R.c = __ldg(p.cost + r0 + lane);
+    }
+}
+
+__device__ __forceinline__ void gen_stage2(const KP& p, int lane, GenRegs& R)
+{
+    if (R.s < 0 || p.m >= 32) return;
+    const long long E0 = __shfl_sync(0xffffffffu, R.rp, 0);
+    const long long E1 = __shfl_sync(0xffffffffu, R.rp, p.m);
+    if (E1 - E0 > 32) return;
+    int lo = 0, hi = (int)(E1 - E0);
+    if (R.pi_s >= 0) {
+        lo = (int)(__shfl_sync(0xffffffffu, R.rp, R.pi_s) - E0);
+        hi = (int)(__shfl_sync(0xffffffffu, R.rp, R.pi_s + 1) - E0);
+    }
+    if (lane >= lo && lane < hi) {
+        R.pr = __ldcs(p.prob + E0 + lane);
+        R.col = __ldcs(p.col + E0 + lane);
+        R.has = true;
+    }
+}
+
+template <bool ARG>
+__device__ __forceinline__ Best gen_eval(const KP& p, const GenRegs& R, const float* __restrict__ A, int lane)
+{
+    Best cur = {kInf, 0x7fffffff, kInf};
+    if (R.s < 0) return cur;
+    if (p.m < 32) {
+        const long long E0 = __shfl_sync(0xffffffffu, R.rp, 0);
+        const long long E1 = __shfl_sync(0xffffffffu, R.rp, p.m);
+        if (E1 - E0 <= 32) {
+            const uint32_t nm1 = (uint32_t)(p.n - 1);
+            const long long nxt = __shfl_down_sync(0xffffffffu, R.rp, 1);
+            const int len = lane < p.m ? (int)(nxt - R.rp) : 0;
+            uint32_t starts = len > 0 ? (1u << (int)(R.rp - E0)) : 0u;   // heads of non-empty rows
+            for (int off = 16; off > 0; off >>= 1) starts |= __shfl_xor_sync(0xffffffffu, starts, off);
+            float x = R.has ? R.pr * gather(A, R.col, nm1) : 0.f;
+            // inclusive scan within rows: add the value d lanes down unless a row starts in between
+            for (int d = 1; d < 32; d <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= d && ((starts >> (lane - d + 1)) & ((1u << d) - 1u)) == 0u) x += y;
+            }
+            const float sum = __shfl_sync(0xffffffffu, x, len > 0 ? (int)(nxt - E0) - 1 : 0);
+            if (R.pi_s >= 0 ? lane == R.pi_s : lane < p.m) {
+                cur.a = lane;
+                cur.q = (R.c == kInf) ? kInf : fmaf(p.gamma, len > 0 ? sum : 0.f, R.c);
+            }
+            for (int off = 16; off > 0; off >>= 1) cur = better(cur, shfl_xor_best<ARG>(cur, off));
+            return cur;
+        }
+    }
+    return csr_gen_state<ARG>(p, R.s, R.pi_s, true, A, lane);
+}
+
+struct GenCarry {
+    GenRegs R0;         // first step of the warp: rows and entries loaded
+    GenRegs R1;         // second step: rows loaded
+    int block_states;   // this lane's state for step `lane` of the first block
+    bool valid;
+};
+
+// the states of steps j0 .. j0+31 of this warp (lane L: step j0 + L)
+__device__ __forceinline__ int gen_resolve(int warp, int U, int j0, int lane, int pos0, int len, const PermKey* K,
+                                           bool* perm_ok)
+{
+    const int pos = warp + (j0 + lane) * U;
+    if (pos >= len) return -1;
+    return K ? state_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
+}
+
+// between the arrival at and the wait on a barrier: load this warp's first two steps of a batch
+template <int KIND>
+__device__ __forceinline__ void gen_prefetch_first(const KP& p, const GroupView& gv, int pos0, int len,
+                                                   const PermKey* K, GenCarry& carry, bool* perm_ok)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (gv.rank * (int)blockDim.x + (int)threadIdx.x) >> 5;
+    const int U = (gv.size * (int)blockDim.x) >> 5;
+    carry.valid = false;
+    if (warp >= len) return;
+    carry.block_states = gen_resolve(warp, U, 0, lane, pos0, len, K, perm_ok);
+    gen_stage1<KIND>(p, __shfl_sync(0xffffffffu, carry.block_states, 0), lane, carry.R0, nullptr);
+    gen_stage1<KIND>(p, __shfl_sync(0xffffffffu, carry.block_states, 1), lane, carry.R1, nullptr);
+    gen_stage2(p, lane, carry.R0);
+    carry.valid = true;
+}
+
+template <int KIND>
+__device__ void csr_batch_gen(const KP& p, const GroupView& gv, const float* __restrict__ A, float* B, int pos0,
+                              int len, const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc,
+                              bool* perm_ok, GenCarry& carry)
+{
+    constexpr bool ARG = (KIND == K_GREEDY);
+    const int lane = threadIdx.x & 31;
+    const int warp = (gv.rank * (int)blockDim.x + (int)threadIdx.x) >> 5;
+    const int U = (gv.size * (int)blockDim.x) >> 5;
+    if (warp >= len) { carry.valid = false; return; }
+    // the old values can load with the rows unless the batch writes where it reads (asynchronous)
+    const float* Aold = (A == B) ? nullptr : A;
+    int block_states;
+    GenRegs r0, r1, r2;
+    if (carry.valid) {
+        block_states = carry.block_states;
+        r0 = carry.R0;
+        r1 = carry.R1;
+    } else {
+        block_states = gen_resolve(warp, U, 0, lane, pos0, len, K, perm_ok);
+        gen_stage1<KIND>(p, __shfl_sync(0xffffffffu, block_states, 0), lane, r0, Aold);
+        gen_stage1<KIND>(p, __shfl_sync(0xffffffffu, block_states, 1), lane, r1, Aold);
+        gen_stage2(p, lane, r0);
+    }
+    carry.valid = false;
+    for (int j = 0; warp + j * U < len; ++j) {
+        const int j2 = j + 2;
+        int s2 = -1;
+        if (warp + j2 * U < len) {
+            if ((j2 & 31) == 0) block_states = gen_resolve(warp, U, j2, lane, pos0, len, K, perm_ok);
+            s2 = __shfl_sync(0xffffffffu, block_states, j2 & 31);
+        }
+        gen_stage1<KIND>(p, s2, lane, r2, Aold);
+        gen_stage2(p, lane, r1);
+        const Best r = gen_eval<ARG>(p, r0, A, lane);
+        if (r0.s >= 0 && lane == 0)
+            state_epilogue_old<KIND>(p, r, r0.s, warp + j * U, r0.has_old ? r0.old : ld_l2(A + r0.s), B, Sout,
+                                     Wout, C, acc);
+        r0 = r1;
+        r1 = r2;
     }
 }
 
@@ -1077,6 +1216,7 @@ struct Runner {
     {
         carry_a.valid = false;
         carry_o.valid = false;
+        carry_g.valid = false;
     }
 
     __device__ bool sync(int site)
@@ -1102,6 +1242,7 @@ struct Runner {
     static constexpr int NCA_ = NCA > 0 ? NCA : 1;
     static constexpr int NCO_ = NCO > 0 ? NCO : 1;
     Carry<NCA_> carry_a;    // prefetched first state of the next min-over-actions batch
+    GenCarry carry_g;       // generic path: prefetched first steps of the next batch
     Carry<NCO_> carry_o;    // ... of the next policy-row batch
     uint64_t wtot = 0;      // RMB_SELECT_WEIGHTED: sum of the weights (read at set-up)
 
@@ -1132,7 +1273,12 @@ struct Runner {
                                                                          acc, &perm_ok, carry_a);
                 return true;
             }
-            csr_batch<KIND, PATH == PATH_CSR_VEC>(p, gv, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
+            if (PATH == PATH_CSR_GEN) {
+                carry_g.valid = carry_g.valid && KIND != K_GREEDY;
+                csr_batch_gen<KIND>(p, gv, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok, carry_g);
+                return true;
+            }
+            csr_batch<KIND, true>(p, gv, lps, A, B, pos0, len, K, So, Wo, C, acc, &perm_ok);
             return true;
         }
     }
@@ -1141,6 +1287,10 @@ struct Runner {
     template <int KIND>
     __device__ void prefetch_next(int pos0, int len, const PermKey* K)
     {
+        if (PATH == PATH_CSR_GEN && KIND != K_GREEDY) {
+            gen_prefetch_first<KIND>(p, gv, pos0, len, K, carry_g, &perm_ok);
+            return;
+        }
         if (PATH != PATH_CSR_VEC) return;
         if (KIND == K_POLICY && NCO > 0)
             fast_prefetch_first<K_POLICY, NCO_>(p, gv, p.lps_one, pos0, len, K, carry_o, &perm_ok);
@@ -1318,6 +1468,7 @@ struct Runner {
         Acc acc = {0.f, kInf, -kInf};
         const float* A = p.d[cur];
         carry_a.valid = false;
+        carry_g.valid = false;
         if (!batch<K_GREEDY>(A, nullptr, 0, p.n, nullptr, nullptr, nullptr, acc)) return false;
         if (next_k >= 0) compute_perm(next_k);
         publish(c, slot, acc, rs);
@@ -1479,7 +1630,7 @@ __global__ void __launch_bounds__(kCsrThreads, 1) rmb_csr_vec_kernel(KP p)
     R.run();
 }
 
-__global__ void __launch_bounds__(kCsrThreads, 2) rmb_csr_gen_kernel(KP p)
+__global__ void __launch_bounds__(kCsrThreads, 1) rmb_csr_gen_kernel(KP p)
 {
     __shared__ RedSmem rs;
     Runner<PATH_CSR_GEN> R(p, rs, nullptr, nullptr, GroupView{(int)blockIdx.x, (int)gridDim.x});
