@@ -736,6 +736,8 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
     oracle.mbvi(m100, 512, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=k512)
     ct = time.perf_counter() - t0
     best = next(r for r in rows if r["mdp"] == "maze100" and r["scheme"] == "vi" and r["b"] == 512)
+    pbytes = m100.prob.nbytes + m100.col.nbytes + m100.row_ptr.nbytes + m100.cost.nbytes
+    ach = best["sweeps"] * pbytes / (best["ms"] / 1e3) / 1e9
     return _line("2D-maze MB-VI time to ||V - J*||_inf <= 1e-4 (N=100, b=512)", 1e3 / best["ms"], "solves/s",
                  best["ms"], args, world,
                  {"workload": "2D-maze stand-ins N=80 (6166 states) and N=100 (9706 states), 4 actions, slip 0.2, "
@@ -743,7 +745,10 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
                               "and asynchronous sweeps; MB-MPI K=50 for b in {1,512,n} (N=100)",
                   "table": rows, "reference_solutions": lines, "paper_speedups_gtx1650ti": PAPER_MAZE,
                   "l2": "P is < 3 MB: L2-resident (latency-bound workload)"},
-                 roofline=None,
+                 roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "traffic": None, "kernel": "rmb_csr_gen_kernel", "peak_kind": peak_kind,
+                           "note": "latency-bound: P (2.6 MB) is L2-resident; a batch costs a barrier plus a "
+                                   "few dependent L2 round trips, so HBM is not the bound"},
                  cpu_baseline={"value": 1.0 / ct, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
                                "sample": f"N=100 maze, b=512, {k512} sweeps, {ct:.2f} s"})
 
@@ -846,12 +851,29 @@ def _select(args, world, rmb, torch, stream, hbm, peak_kind):
         rows.append({"mdp": "maze100 warm start", "b": b, "selection": label + (f" refresh={refresh}" if refresh else ""),
                      "ms": round(min(ts), 3), "sweeps": hi, "err": err()})
     best = next(r for r in rows if r["mdp"] == "csr2e20" and r["b"] == 262144 and r["selection"] == "uniform")
+    # the FP64 oracle on the host cores: uniform-draw sweeps of the same MDP (bounded sample)
+    import oracle
+    Vc = np.zeros(mdp.n)
+    t0 = time.perf_counter()
+    csw = 0
+    while csw < 50 and time.perf_counter() - t0 < 10.0:
+        Vc = oracle.mbvi(mdp, 262144, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=1, V0=Vc, start_sweep=csw,
+                         select=1)["V"]
+        csw += 1
+    ct = time.perf_counter() - t0
+    ach = best["sweeps"] * sweep_bytes(mdp.n, M_ACTIONS, K_SUCC) / (best["ms"] / 1e3) / 1e9
     return _line("batch selection with replacement: CSR n=2^20 MB-VI to 1e-6 with uniform draws (b=262144)",
                  mdp.n * best["sweeps"] / (best["ms"] / 1e3), "Bellman backups/s", best["ms"], args, world,
                  {"workload": "csr-mdp n=2^20 m=8 k=32 gamma=0.99 (sigma / uniform draws / residual-weighted draws, "
                               "b in {16384, 262144}); maze N=100 warm start after a 10x10 cost block rises 1 -> 3",
                   "table": rows, "maze_initial_err": init_err, "maze_block_states": int(len(block))},
-                 roofline=None, cpu_baseline=None)
+                 roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "traffic": None, "kernel": "rmb_csr_vec_kernel (draws)", "peak_kind": peak_kind,
+                           "note": "P stream per sweep x sweeps / solve time; bound by random successor gathers "
+                                   "as the sigma solve"},
+                 cpu_baseline={"value": mdp.n * csw / ct, "unit": "Bellman backups/s", "cores": oracle.num_threads(),
+                               "kind": "oracle", "sample": f"{csw} uniform-draw MB-VI sweeps (b=262144) of the "
+                                                           f"n=2^20 MDP from V=0, FP64, {ct:.1f} s"})
 
 
 if __name__ == "__main__":
