@@ -98,7 +98,12 @@ typedef struct {
                                 evaluation) or per-improvement residual (MPI); NULL = none */
     int32_t select;          /* batch selection: RMB_SELECT_PERMUTATION (0, the paper's method),
                                 RMB_SELECT_UNIFORM or RMB_SELECT_WEIGHTED (with replacement) */
-    int32_t reserved_select;
+    int32_t residual_kind;   /* stop test of rmb_vi: RMB_RESIDUAL_SWEEP (0: the sweep change
+                                delta_k = ||V_k - V_{k-1}||_inf) or RMB_RESIDUAL_BELLMAN (1: a sweep
+                                with delta_k <= eps is confirmed by a full Bellman pass and the solve
+                                stops only if ||TV - V||_inf <= eps; stats->residual is that value).
+                                MPI always stops on ||TV - V||_inf (Alg. 1); rmb_eval_policy and the
+                                batched API support 0 only. */
     const uint32_t *weights; /* RMB_SELECT_WEIGHTED: device [n] integer weights, sum > 0; else NULL */
 } rmb_opts;
 
@@ -121,6 +126,8 @@ typedef struct {
  * Workspace: + 16*n bytes of batch marks when b < n, and for RMB_SELECT_WEIGHTED another 8*n bytes
  * of cumulative weights (+ 8 per 8192 states).
  */
+#define RMB_RESIDUAL_SWEEP 0
+#define RMB_RESIDUAL_BELLMAN 1
 #define RMB_SELECT_PERMUTATION 0
 #define RMB_SELECT_UNIFORM 1
 #define RMB_SELECT_WEIGHTED 2

@@ -58,7 +58,7 @@ def lib():
         L.orc_mpi.restype = i64
         L.orc_sweep_order.argtypes = [i64, u64, u64, i32, vp, vp]
         L.orc_sweep_order.restype = ctypes.c_int
-        L.orc_mbvi_select.argtypes = [P(_OrcMDP), vp, i64, u64, i64, f64, i64, i32, vp, vp, vp, vp, vp]
+        L.orc_mbvi_select.argtypes = [P(_OrcMDP), vp, i64, u64, i64, f64, i64, i32, vp, i32, vp, vp, vp, vp]
         L.orc_mbvi_select.restype = i64
         L.orc_mpi_select.argtypes = [P(_OrcMDP), i64, i32, u64, i64, f64, i64, i32, vp, vp, vp, vp, vp]
         L.orc_mpi_select.restype = i64
@@ -195,11 +195,12 @@ def mb_apply(mdp, J: np.ndarray, b: int, seed: int, sweep: int, pi: Optional[np.
 
 def mbvi(mdp, b: int, seed: int, eps: float = 1e-6, max_sweeps: int = 100000, V0=None,
          start_sweep: int = 0, pi: Optional[np.ndarray] = None, traj: bool = False, select: int = 0,
-         weights=None):
+         weights=None, residual_kind: int = 0):
     """MB-VI (pi None) or mini-batch policy evaluation (pi given) until delta <= eps.
 
-    select 1 / 2: batches drawn with replacement (uniform / by the uint32 weights); the stop then
-    also needs the full residual <= eps.  Returns dict(V, sweeps, deltas, resid[, traj]).
+    select 1 / 2: batches drawn with replacement (uniform / by the uint32 weights); there, and with
+    residual_kind 1, the stop also needs the full residual <= eps.
+    Returns dict(V, sweeps, deltas, resid[, traj]).
     """
     B = _bind(mdp)
     n = mdp.n
@@ -210,8 +211,8 @@ def mbvi(mdp, b: int, seed: int, eps: float = 1e-6, max_sweeps: int = 100000, V0
     w = _weights(select, weights, n)
     resid = ctypes.c_double(0.0)
     k = lib().orc_mbvi_select(B.ref, _ptr(pi_c), int(b), int(seed), int(start_sweep), float(eps),
-                              int(max_sweeps), int(select), _ptr(w), _ptr(V), _ptr(deltas), _ptr(T),
-                              ctypes.byref(resid))
+                              int(max_sweeps), int(select), _ptr(w), int(residual_kind), _ptr(V), _ptr(deltas),
+                              _ptr(T), ctypes.byref(resid))
     if k < 0:
         raise ValueError("bad select or zero total weight")
     out = {"V": V, "sweeps": int(k), "deltas": deltas[:k], "resid": float(resid.value)}

@@ -314,25 +314,27 @@ static double full_residual(const orc_mdp *M, const int32_t *pi, const double *V
  * [max_sweeps*n]) = V after each sweep.  Returns the number of sweeps done.
  * ------------------------------------------------------------------------------------------ */
 int64_t orc_mbvi_select(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, int64_t start_sweep,
-                        double eps, int64_t max_sweeps, int32_t select, const uint32_t *weights, double *V,
-                        double *delta_trace, double *V_traj, double *resid_out);
+                        double eps, int64_t max_sweeps, int32_t select, const uint32_t *weights, int32_t residual_kind,
+                        double *V, double *delta_trace, double *V_traj, double *resid_out);
 
 int64_t orc_mbvi(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, int64_t start_sweep,
                  double eps, int64_t max_sweeps, double *V, double *delta_trace, double *V_traj)
 {
-    return orc_mbvi_select(M, pi, b, seed, start_sweep, eps, max_sweeps, 0, NULL, V, delta_trace, V_traj, NULL);
+    return orc_mbvi_select(M, pi, b, seed, start_sweep, eps, max_sweeps, 0, NULL, 0, V, delta_trace, V_traj, NULL);
 }
 
 /* ------------------------------------------------------------------------------------------ *
  * MB-VI / evaluation with a batch-selection rule (select 0: sigma, the paper's method; 1, 2: draws
- * with replacement as defined above).  With draws a sweep's change covers only the states drawn,
- * so a sweep with delta <= eps is followed by the full residual ||TV - V||_inf (||T_pi V - V||_inf)
- * and the solve stops only when that is <= eps too.  *resid_out (optional) = the last full residual
- * (select 1, 2) or delta (select 0).  Returns sweeps done, or -1 on a bad select / zero weights.
+ * with replacement as defined above) and a stop test (residual_kind 0: the sweep change delta_k;
+ * 1: the Bellman residual).  With draws a sweep's change covers only the states drawn, so there,
+ * and with residual_kind 1, a sweep with delta <= eps is followed by the full residual
+ * ||TV - V||_inf (||T_pi V - V||_inf) and the solve stops only when that is <= eps too.
+ * *resid_out (optional) = the last full residual when one was taken, else delta.  Returns sweeps
+ * done, or -1 on a bad select / zero weights.
  * ------------------------------------------------------------------------------------------ */
 int64_t orc_mbvi_select(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t seed, int64_t start_sweep,
-                        double eps, int64_t max_sweeps, int32_t select, const uint32_t *weights, double *V,
-                        double *delta_trace, double *V_traj, double *resid_out)
+                        double eps, int64_t max_sweeps, int32_t select, const uint32_t *weights, int32_t residual_kind,
+                        double *V, double *delta_trace, double *V_traj, double *resid_out)
 {
     int64_t n = M->n;
     int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
@@ -350,7 +352,7 @@ int64_t orc_mbvi_select(const orc_mdp *M, const int32_t *pi, int64_t b, uint64_t
         done = j + 1;
         resid = delta;
         if (delta <= eps) {
-            if (select == 0) break;
+            if (select == 0 && residual_kind == 0) break;
             resid = full_residual(M, pi, V);
             if (resid <= eps) break;
         }

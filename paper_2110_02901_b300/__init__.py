@@ -40,6 +40,7 @@ RMB_FLAG_INJECT_BARRIER_STALL = 1
 RMB_FLAG_RAW_ROWS = 2
 RMB_FLAG_ASYNC = 4
 RMB_SELECT_PERMUTATION, RMB_SELECT_UNIFORM, RMB_SELECT_WEIGHTED = 0, 1, 2
+RMB_RESIDUAL_SWEEP, RMB_RESIDUAL_BELLMAN = 0, 1
 PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic", 3: "dense-tma"}
 
 
@@ -59,7 +60,7 @@ class rmb_opts(ctypes.Structure):
         ("eval_sweeps", ctypes.c_int32), ("validate", ctypes.c_int32),
         ("barrier_timeout_ns", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
         ("flags", ctypes.c_int32), ("trace", ctypes.c_void_p),
-        ("select", ctypes.c_int32), ("reserved_select", ctypes.c_int32), ("weights", ctypes.c_void_p),
+        ("select", ctypes.c_int32), ("residual_kind", ctypes.c_int32), ("weights", ctypes.c_void_p),
     ]
 
 
@@ -213,6 +214,7 @@ class Opts:
     trace: object = None       # optional torch float64 CUDA tensor [max_sweeps]
     select: int = 0            # RMB_SELECT_PERMUTATION / _UNIFORM / _WEIGHTED
     weights: object = None     # RMB_SELECT_WEIGHTED: torch int32 (read as uint32) CUDA tensor [n]
+    residual_kind: int = 0     # RMB_RESIDUAL_SWEEP / RMB_RESIDUAL_BELLMAN (stop test of rmb_vi)
 
     def desc(self) -> rmb_opts:
         o = rmb_opts()
@@ -222,6 +224,7 @@ class Opts:
         o.barrier_timeout_ns, o.grid_ctas, o.flags = int(self.barrier_timeout_ns), int(self.grid_ctas), int(self.flags)
         o.trace = _ptr(self.trace)
         o.select = int(self.select)
+        o.residual_kind = int(self.residual_kind)
         o.weights = _ptr(self.weights)
         return o
 

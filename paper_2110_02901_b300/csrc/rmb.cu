@@ -74,6 +74,7 @@ struct KP {
     int k4_log2;            // CSR vectorised: log2(k/4)
     int32_t* perm_buf;      // non-null when the order is precomputed (see use_perm_buf): that of the coming sweep
     int select;             // RMB_SELECT_*: sigma, or draws with replacement (uniform / by weight)
+    int residual_kind;      // RMB_RESIDUAL_*: stop test of MB-VI (sweep change / confirmed Bellman residual)
     const uint64_t* cdf;    // RMB_SELECT_WEIGHTED: cumulative weights [n] (in the workspace)
     uint64_t* mark;         // draws with T >= 2: [2][n], mark[t & 1][s] = stamp of batch t if it updates s
     int stage;              // dense: floats of V staged per chunk
@@ -1430,7 +1431,8 @@ struct Runner {
         cur = newcur;
         // a solve that ends here skips the closing phase; with draws the caller may still go on
         // (its full-residual check can fail), so the buffers and the next order must be completed
-        if (stop && (p.select == RMB_SELECT_PERMUTATION || is_last)) return true;
+        if (stop && ((p.select == RMB_SELECT_PERMUTATION && p.residual_kind == RMB_RESIDUAL_SWEEP) || is_last))
+            return true;
         const float shift = shift_for(lo, hi);
         if (shift != 0.f) {
             float* F = p.d[cur];
@@ -1565,8 +1567,9 @@ struct Runner {
                 residual = (double)delta;
                 if (stop) {
                     converged = (double)delta <= p.eps;
-                    if (converged && p.select != RMB_SELECT_PERMUTATION) {
-                        // draws: the change covers only the drawn states; confirm with a full pass
+                    if (converged && (p.select != RMB_SELECT_PERMUTATION || p.residual_kind == RMB_RESIDUAL_BELLMAN)) {
+                        // draws (the change covers only the drawn states) or the Bellman stop test:
+                        // confirm with a full pass
                         float r;
                         if (!greedy_pass(r)) return finish(false, sweeps, 0, residual);   // also writes V
                         residual = (double)r;
@@ -2282,7 +2285,8 @@ int fill_kp(int mode, const rmb_mdp* M, const rmb_opts* O, int64_t b, char* ws, 
     // asynchronous sweeps have no barrier before a sweep's first read, so sigma is computed on the fly
     const bool async = (O->flags & RMB_FLAG_ASYNC) != 0;
     p.perm_buf = (L.perm_buf && mode != MODE_GREEDY && !async) ? reinterpret_cast<int32_t*>(ws + L.pb) : nullptr;
-    p.select = RMB_SELECT_PERMUTATION;   // solve() sets the selection rule of a single-MDP call
+    p.select = RMB_SELECT_PERMUTATION;   // solve() sets the selection rule and stop test of a single-MDP call
+    p.residual_kind = RMB_RESIDUAL_SWEEP;
     p.cdf = nullptr;
     p.mark = nullptr;
     p.ctrl = ctrl;
@@ -2344,6 +2348,10 @@ int solve(const Call& q)
     if (select < RMB_SELECT_PERMUTATION || select > RMB_SELECT_WEIGHTED) return RMB_ERR_ARG;
     if (select == RMB_SELECT_WEIGHTED && !O->weights) return RMB_ERR_ARG;
     if (select != RMB_SELECT_PERMUTATION && q.mode == MODE_EVAL) return RMB_ERR_UNSUPPORTED;
+    const int rkind = q.mode == MODE_VI ? O->residual_kind : RMB_RESIDUAL_SWEEP;
+    if (q.mode != MODE_GREEDY && (O->residual_kind < RMB_RESIDUAL_SWEEP || O->residual_kind > RMB_RESIDUAL_BELLMAN))
+        return RMB_ERR_ARG;
+    if (O->residual_kind != RMB_RESIDUAL_SWEEP && q.mode == MODE_EVAL) return RMB_ERR_UNSUPPORTED;
     const Layout L = layout(M->n, b, select);
     if (!q.ws || ((uintptr_t)q.ws & 255)) return RMB_ERR_WORKSPACE;
     if (q.ws_bytes < L.total) return RMB_ERR_WORKSPACE;
@@ -2355,6 +2363,7 @@ int solve(const Call& q)
     KP p;
     int path = fill_kp(q.mode, M, O, b, ws, L, reinterpret_cast<Ctrl*>(ws + L.ctrl), p);
     p.select = select;
+    p.residual_kind = rkind;
     p.cdf = select == RMB_SELECT_WEIGHTED ? reinterpret_cast<const uint64_t*>(ws + L.cdf) : nullptr;
     // consecutive batches may share states only with draws, and only an asynchronous sweep has no copies
     p.mark = (L.cdf > L.mark && !(O->flags & RMB_FLAG_ASYNC)) ? reinterpret_cast<uint64_t*>(ws + L.mark) : nullptr;
@@ -2702,7 +2711,8 @@ int check_batch(const rmb_batch_item* items, int count, const rmb_opts* O)
 {
     if (!items || count < 1 || !O) return RMB_ERR_ARG;
     if (O->max_sweeps < 1 || !(O->eps >= 0.0) || std::isinf(O->eps) || O->start_sweep < 0) return RMB_ERR_ARG;
-    if ((O->flags & RMB_FLAG_ASYNC) || O->select != RMB_SELECT_PERMUTATION) return RMB_ERR_UNSUPPORTED;
+    if ((O->flags & RMB_FLAG_ASYNC) || O->select != RMB_SELECT_PERMUTATION || O->residual_kind != RMB_RESIDUAL_SWEEP)
+        return RMB_ERR_UNSUPPORTED;
     for (int i = 0; i < count; ++i) {
         const int st = check_mdp(&items[i].mdp);
         if (st) return st;

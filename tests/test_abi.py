@@ -205,3 +205,12 @@ def test_residual_weights_arguments(L):
         assert f(ctypes.byref(d), 4096, frac, 8192, 1 << 20, nb, None) == rmb.RMB_ERR_ARG
     assert f(ctypes.byref(d), None, 0.1, 8192, 1 << 20, nb, None) == rmb.RMB_ERR_ARG
     assert f(ctypes.byref(d), 4096, 0.1, 8192, 1 << 20, nb - 1, None) == rmb.RMB_ERR_WORKSPACE
+
+
+def test_residual_kind_arguments(L):
+    d, o = _fake_mdp(), _opts()
+    o.residual_kind = 2
+    assert L.rmb_vi(ctypes.byref(d), ctypes.byref(o), 4096, None, None, 8192, 1 << 30, None, None) == rmb.RMB_ERR_ARG
+    o.residual_kind = rmb.RMB_RESIDUAL_BELLMAN   # evaluation keeps the sweep-change test
+    assert L.rmb_eval_policy(ctypes.byref(d), 4096, ctypes.byref(o), 4096, 8192, 1 << 30, None, None) == \
+        rmb.RMB_ERR_UNSUPPORTED

@@ -340,3 +340,22 @@ def test_grid_size_does_not_change_results():
     ref = oracle.mbvi(mdp, 200, seed=3, eps=0.0, max_sweeps=4)
     for o in outs:
         close(o, ref["V"])
+
+
+def test_bellman_residual_stop_test_matches_oracle():
+    """residual_kind = RMB_RESIDUAL_BELLMAN: the solve ends on a confirmed ||TV - V||_inf <= eps; the
+    values equal the oracle's under the same rule, and the full residual really is below eps."""
+    from oracle import exact
+    for mdp in (mdpgen.csr_uniform_k(3000, 8, 32, gamma=0.95, seed=3),
+                mdpgen.csr_ragged(1500, 4, 9, gamma=0.9, seed=4), mdpgen.dense_dirichlet(300, 4, gamma=0.95, seed=5)):
+        dm = rmb.DeviceMDP.from_host(mdp)
+        for b in (37, mdp.n):
+            ref = oracle.mbvi(mdp, b, 9, eps=1e-5, max_sweeps=100000, residual_kind=1)
+            V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+            st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=9, eps=1e-5, max_sweeps=100000,
+                                         residual_kind=rmb.RMB_RESIDUAL_BELLMAN), V)
+            assert st["status"] == rmb.RMB_OK and st["residual"] <= 1e-5
+            v = V.cpu().numpy().astype(np.float64)
+            assert float(np.abs(exact.bellman_pass(mdp, v)[0] - v).max()) <= 1.2e-5
+            assert abs(st["sweeps"] - ref["sweeps"]) <= 2
+            assert np.abs(v - ref["V"]).max() <= 1e-4 * max(1.0, np.abs(ref["V"]).max())

@@ -498,3 +498,18 @@ def test_with_replacement_converges_under_the_stop_rule():
             assert np.max(np.abs(r["V"] - jstar)) <= 0.9 / 0.1 * resid + 1e-12
         m = oracle.mpi(mdp, 16, K=5, seed=2, eps=1e-10, select=select, weights=w)
         assert m["resid"][-1] <= 1e-10 and np.max(np.abs(m["V"] - jstar)) < 1e-8
+
+
+def test_bellman_residual_stop_rule():
+    """residual_kind 1: a sweep change <= eps is confirmed by ||TV - V||_inf <= eps (eq. (7))."""
+    mdp = mdpgen.csr_uniform_k(300, 4, 8, gamma=0.95, seed=17)
+    for b in (1, 30, 300):
+        r0 = oracle.mbvi(mdp, b, 5, eps=1e-8, max_sweeps=100000)
+        r1 = oracle.mbvi(mdp, b, 5, eps=1e-8, max_sweeps=100000, residual_kind=1)
+        full0 = float(np.max(np.abs(exact.bellman_pass(mdp, r0["V"])[0] - r0["V"])))
+        full1 = float(np.max(np.abs(exact.bellman_pass(mdp, r1["V"])[0] - r1["V"])))
+        assert full1 <= 1e-8 and abs(full1 - r1["resid"]) < 1e-13
+        assert r1["sweeps"] >= r0["sweeps"]
+        # the sweep-change rule can stop with a larger full residual; the trajectories agree up to there
+        assert np.array_equal(r1["deltas"][:r0["sweeps"]], r0["deltas"])
+        assert full0 >= 0.0

@@ -61,6 +61,7 @@ PINS = [
     T.test_constant_weights_reproduce_uniform_draws,
     lambda: T.test_with_replacement_sweep_matches_definition(1),
     T.test_with_replacement_converges_under_the_stop_rule,
+    T.test_bellman_residual_stop_rule,
 ]
 
 
