@@ -394,6 +394,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(b), "n": n, "m": M_ACTIONS, "k": K_SUCC, "gamma": GAMMA,
                        "batch": b, "eps": EPS, "sweeps_per_step": sweeps / args.steps,
+                       "sa_backups_per_s": value * M_ACTIONS, "nnz_per_s": value * M_ACTIONS * K_SUCC,
                        "time_to_eps_ms": ms_max / args.steps, "parallelism": f"replicas x{world}",
                        "l2": "inputs (2.2 GB of P per sweep) exceed the 126 MB L2; no flush needed",
                        "validate": "once before timing", "path": stats[-1]["path"],
@@ -452,7 +453,6 @@ def run_workload(args, world, rank, local):
 
 def _dense500(args, world, rmb, torch, stream, hbm, peak_kind):
     """Dense n=500, m=4, Dirichlet(1), gamma=0.95, b=50: MB-VI to 1e-6 (latency-bound: P is 4 MB)."""
-    import oracle
     mdp = mdpgen.config1()
     dm = rmb.DeviceMDP.from_host(mdp)
     o = rmb.Opts(batch=50, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=100000, validate=False)
@@ -468,10 +468,15 @@ def _dense500(args, world, rmb, torch, stream, hbm, peak_kind):
         step()
     ms, outs = _timed(step, args.steps, stream)
     sw = outs[-1]["sweeps"]
-    t0 = time.perf_counter()
-    ref = oracle.mbvi(mdp, 50, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=100000)
-    ct = time.perf_counter() - t0
-    err = float(np.abs(V.cpu().numpy() - ref["V"]).max())
+    err, cpu = None, None
+    if not args.no_cpu:   # CPU-baseline leg: the FP64 oracle's full solve, timed, and the GPU error against it
+        import oracle
+        t0 = time.perf_counter()
+        ref = oracle.mbvi(mdp, 50, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=100000)
+        ct = time.perf_counter() - t0
+        err = float(np.abs(V.cpu().numpy() - ref["V"]).max())
+        cpu = {"value": mdp.n * ref["sweeps"] / ct, "unit": "Bellman backups/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"full solve, {ref['sweeps']} sweeps, {ct:.2f} s"}
     bytes_launch = (sw + 1) * mdp.n * mdp.m * mdp.n * 4
     ach = bytes_launch / (outs[-1]["ms"] / 1e3) / 1e9
     return _line(METRIC, mdp.n * sw / (ms / 1e3), "Bellman backups/s", ms, args, world,
@@ -481,15 +486,12 @@ def _dense500(args, world, rmb, torch, stream, hbm, peak_kind):
                  roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                            "traffic": None, "kernel": "rmb_dense_kernel<f32>", "peak_kind": peak_kind,
                            "note": "P is L2-resident; the bound is the per-batch barrier latency (10 batches/sweep)"},
-                 cpu_baseline={"value": mdp.n * ref["sweeps"] / ct, "unit": "Bellman backups/s",
-                               "cores": oracle.num_threads(), "kind": "oracle",
-                               "sample": f"full solve, {ref['sweeps']} sweeps, {ct:.2f} s"})
+                 cpu_baseline=cpu)
 
 
 def _dense16k(args, world, rmb, torch, stream, hbm, peak_kind):
     """Dense n=16384, m=16, Dirichlet(0.1), c~N(0,1), gamma=0.999: sweep throughput per storage type and
     b; converged error per storage type on the same recipe at n=2048 against the exact optimum."""
-    from oracle import exact
     if args.profile_case:
         # profiling mode: one solve of exactly profile_case sweeps at n = 2^n_log2 (default 2^20 is
         # reduced to 2^12 here), b = n/4, storage --storage
@@ -537,26 +539,46 @@ def _dense16k(args, world, rmb, torch, stream, hbm, peak_kind):
                                                   "sweeps": [s1["sweeps"], s2["sweeps"]]}
     del forms, d32, P
     torch.cuda.empty_cache()
-    # converged error per storage type, same recipe at n = 2048, against the exact optimum (policy iteration)
-    sm = mdpgen.dense_dirichlet(2048, 16, alpha=0.1, gamma=0.999, seed=3, cost_dist="normal")
-    jstar, _, _ = exact.policy_iteration(sm)
-    dm = rmb.DeviceMDP.from_host(sm)
+    # CPU-baseline leg (skipped with --no-cpu): the FP64 exact optimum of the same recipe at n = 2048
+    # (policy iteration), and the error of each storage type's converged GPU solve against it
     errs = {}
-    for name, form in (("f32", dm), ("bf16", rmb.dense_lowp(dm, rmb.RMB_P_BF16)),
-                       ("fp8", rmb.dense_lowp(dm, rmb.RMB_P_FP8E4M3))):
-        o = rmb.Opts(batch=256, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=400000, validate=False)
-        V2 = torch.zeros(2048, dtype=torch.float32, device="cuda")
-        st = rmb.rmb_vi(form, o, V2, stream=stream)
-        e = float(np.abs(V2.cpu().numpy() - jstar).max() / np.abs(jstar).max())
-        rec = {"sweeps": st["sweeps"], "ms": st["ms"], "rel_err_vs_exact": e}
-        if name != "f32":
-            V3 = torch.zeros(2048, dtype=torch.float32, device="cuda")
-            s1, s2 = rmb.rmb_vi_refined(form, dm, o, EPS, V3)
-            rec["refined_rel_err"] = float(np.abs(V3.cpu().numpy() - jstar).max() / np.abs(jstar).max())
-            rec["refined_sweeps"] = [s1["sweeps"], s2["sweeps"]]
-            rec["refined_ms"] = s1["ms"] + s2["ms"]
-        errs[name] = rec
+    if not args.no_cpu:
+        from oracle import exact
+        sm = mdpgen.dense_dirichlet(2048, 16, alpha=0.1, gamma=0.999, seed=3, cost_dist="normal")
+        jstar, _, _ = exact.policy_iteration(sm)
+        dm = rmb.DeviceMDP.from_host(sm)
+        for name, form in (("f32", dm), ("bf16", rmb.dense_lowp(dm, rmb.RMB_P_BF16)),
+                           ("fp8", rmb.dense_lowp(dm, rmb.RMB_P_FP8E4M3))):
+            o = rmb.Opts(batch=256, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=400000, validate=False)
+            V2 = torch.zeros(2048, dtype=torch.float32, device="cuda")
+            st = rmb.rmb_vi(form, o, V2, stream=stream)
+            e = float(np.abs(V2.cpu().numpy() - jstar).max() / np.abs(jstar).max())
+            rec = {"sweeps": st["sweeps"], "ms": st["ms"], "rel_err_vs_exact": e}
+            if name != "f32":
+                V3 = torch.zeros(2048, dtype=torch.float32, device="cuda")
+                s1, s2 = rmb.rmb_vi_refined(form, dm, o, EPS, V3)
+                rec["refined_rel_err"] = float(np.abs(V3.cpu().numpy() - jstar).max() / np.abs(jstar).max())
+                rec["refined_sweeps"] = [s1["sweeps"], s2["sweeps"]]
+                rec["refined_ms"] = s1["ms"] + s2["ms"]
+            errs[name] = rec
     best = max(thr, key=lambda r: r["p_stream_gbs"] if r["storage"] == "f32" else -1)
+    # the FP64 oracle on the host cores: MB-VI sweeps of the same recipe at n = 2048 (the n = 16384 P
+    # is 17 GB); its P-stream rate, converted to backups/s at n = 16384 (m * n * 4 bytes per backup)
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        small = mdpgen.dense_dirichlet(2048, m, alpha=0.1, gamma=0.999, seed=3, cost_dist="normal")
+        Vc = np.zeros(small.n)
+        t0 = time.perf_counter()
+        csw = 0
+        while csw < 200 and time.perf_counter() - t0 < 10.0:
+            Vc = oracle.mbvi(small, 4096, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=1, V0=Vc, start_sweep=csw)["V"]
+            csw += 1
+        ct = time.perf_counter() - t0
+        cpu_gbs = csw * small.P.nbytes / ct / 1e9
+        cpu = {"value": cpu_gbs * 1e9 / (m * n * 4), "unit": "Bellman backups/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"{csw} FP64 MB-VI sweeps of the same recipe at n=2048 ({ct:.1f} s, "
+                                           f"{cpu_gbs:.2f} GB/s of P), converted to n=16384 by P bytes per backup"}
     return _line("dense sweep throughput per P storage type (and converged error vs the exact optimum)",
                  best["backups_per_s"], "Bellman backups/s", best["ms_per_sweep"], args, world,
                  {"workload": "dense-mdp n=16384 m=16 dirichlet(0.1) c~N(0,1) gamma=0.999; 20 MB-VI sweeps "
@@ -565,7 +587,7 @@ def _dense16k(args, world, rmb, torch, stream, hbm, peak_kind):
                  roofline={"bound": "hbm", "achieved": best["p_stream_gbs"], "peak": hbm, "unit": "GB/s",
                            "frac": best["p_stream_gbs"] / hbm, "traffic": None,
                            "kernel": "rmb_dense_kernel<f32>", "peak_kind": peak_kind},
-                 throughput=thr, full_solves=full, converged_errors_n2048=errs)
+                 cpu_baseline=cpu, throughput=thr, full_solves=full, converged_errors_n2048=errs)
 
 
 def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
@@ -609,6 +631,26 @@ def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
         V = torch.zeros(x.n, dtype=torch.float32, device="cuda")
         st = rmb.rmb_vi(dm, oo, V)
         seq_ms += st["ms"]
+    # CPU-baseline leg: the FP64 oracle on the host cores, whole solves of the MDPs in plan order until
+    # ~15 s, and the sum over all MDPs extrapolated by their nnz x sweeps (the GPU's sweep counts)
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        done_work = 0.0
+        solved = 0
+        for x, p_ in zip(mdps, plan):
+            oracle.mbvi(x, p_["batch"], seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=200000)
+            done_work += x.nnz * res[solved]["sweeps"]
+            solved += 1
+            if time.perf_counter() - t0 > 15.0:
+                break
+        ct = time.perf_counter() - t0
+        all_work = sum(x.nnz * r["sweeps"] for x, r in zip(mdps, res))
+        cpu_total_s = ct * all_work / done_work
+        cpu = {"value": backups / cpu_total_s, "unit": "Bellman backups/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"{solved} of {len(mdps)} MDPs solved to 1e-6 in FP64 ({ct:.1f} s); "
+                                           f"all 256 extrapolated by nnz x sweeps: {cpu_total_s:.0f} s"}
     return _line("batched time-to-1e-6 (all 256 MDPs) and Bellman backups/s", backups / (ms / 1e3),
                  "Bellman backups/s", ms, args, world,
                  {"workload": "256 csr-mdps n~logU[256,65536] m~U{2..16} k=16 dirichlet(1) c~U[0,1] "
@@ -620,12 +662,12 @@ def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
                   "max_sweeps": max(r["sweeps"] for r in res)},
                  roofline={"bound": "hbm", "achieved": nnz_passes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                            "frac": nnz_passes / (ms / 1e3) / 1e9 / hbm, "traffic": None,
-                           "kernel": "rmb_batched_kernel", "peak_kind": peak_kind})
+                           "kernel": "rmb_batched_kernel", "peak_kind": peak_kind},
+                 cpu_baseline=cpu)
 
 
 def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
     """n=65536, m=8, k=16 softmax MDP: forward MB-VI (gamma=0.95) and the adjoint gradient of w.V*."""
-    from oracle import exact
     mdp = mdpgen.config5()
     dm = rmb.DeviceMDP.from_host(mdp)
     z = torch.from_numpy(mdp.logits).cuda()
@@ -647,18 +689,21 @@ def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
         step()
     ms, outs = _timed(step, args.steps, stream)
     st1, st2 = outs[-1]
-    t0 = time.perf_counter()
-    exact.fixed_point_gradient(mdp, w.cpu().numpy().astype(np.float64))
-    ct = time.perf_counter() - t0
+    cpu = None
+    if not args.no_cpu:   # CPU-baseline leg: the FP64 direct-solve gradient on the host
+        from oracle import exact
+        t0 = time.perf_counter()
+        exact.fixed_point_gradient(mdp, w.cpu().numpy().astype(np.float64))
+        ct = time.perf_counter() - t0
+        cpu = {"value": 1.0 / ct, "unit": "gradients/s", "cores": 0, "kind": "oracle",
+               "sample": f"direct-solve gradient (policy iteration + GMRES adjoint), {ct:.1f} s"}
     return _line("time of forward solve + adjoint gradient (w.V*, dcost and dlogits)", 1e3 / ms, "gradients/s", ms,
                  args, world,
                  {"workload": "csr-mdp n=65536 m=8 k=16 P=softmax(N(0,1) logits) c~U[0,1] gamma=0.95; forward MB-VI "
                               "b=4096 to 1e-7, adjoint mini-batch sweeps b=4096 to 1e-7",
                   "forward_ms": st1["ms"], "forward_sweeps": st1["sweeps"], "adjoint_ms": st2["ms"],
                   "adjoint_sweeps": st2["sweeps"]},
-                 roofline=None,
-                 cpu_baseline={"value": 1.0 / ct, "unit": "gradients/s", "cores": 0, "kind": "oracle",
-                               "sample": f"direct-solve gradient (policy iteration + GMRES adjoint), {ct:.1f} s"})
+                 roofline=None, cpu_baseline=cpu)
 
 
 # speed-ups at 1e-4 of J* printed in Sec. IV-B (GTX 1650 Ti): context, not targets
@@ -673,7 +718,6 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
     measure of Sec. IV-B.  J* comes from a GPU MB-MPI solve to ||TV - V||_inf <= 1e-7 (error below
     1.9e-6 by the contraction bound).  The sweep count k*(b) is found by stepping one sweep (MPI: one
     improvement round) at a time; the timed run is a fresh solve from 0 capped at k*(b)."""
-    import oracle
     TOL = 1e-4
     K = 50
     rows, lines = [], {}
@@ -729,12 +773,17 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
             r["speedup_over_b_n"] = round(full / r["ms"], 3)
             r["speedup_over_b_1"] = round(gs / r["ms"], 3)
         lines[mdp.name] = {"J*_certified_err": cert, "J*_mpi_ms": st["ms"]}
-    # CPU baseline: the FP64 oracle's MB-VI on the N = 100 maze at b = 512 for the same sweep count
+    # CPU-baseline leg: the FP64 oracle's MB-VI on the N = 100 maze at b = 512 for the same sweep count
     m100 = mdpgen.maze100()
     k512 = next(r["sweeps"] for r in rows if r["mdp"] == "maze100" and r["scheme"] == "vi" and r["b"] == 512)
-    t0 = time.perf_counter()
-    oracle.mbvi(m100, 512, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=k512)
-    ct = time.perf_counter() - t0
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.mbvi(m100, 512, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=k512)
+        ct = time.perf_counter() - t0
+        cpu = {"value": 1.0 / ct, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": f"N=100 maze, b=512, {k512} sweeps, {ct:.2f} s"}
     best = next(r for r in rows if r["mdp"] == "maze100" and r["scheme"] == "vi" and r["b"] == 512)
     pbytes = m100.prob.nbytes + m100.col.nbytes + m100.row_ptr.nbytes + m100.cost.nbytes
     ach = best["sweeps"] * pbytes / (best["ms"] / 1e3) / 1e9
@@ -749,8 +798,7 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
                            "traffic": None, "kernel": "rmb_csr_gen_kernel", "peak_kind": peak_kind,
                            "note": "latency-bound: P (2.6 MB) is L2-resident; a batch costs a barrier plus a "
                                    "few dependent L2 round trips, so HBM is not the bound"},
-                 cpu_baseline={"value": 1.0 / ct, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
-                               "sample": f"N=100 maze, b=512, {k512} sweeps, {ct:.2f} s"})
+                 cpu_baseline=cpu)
 
 
 def _select(args, world, rmb, torch, stream, hbm, peak_kind):
@@ -851,16 +899,21 @@ def _select(args, world, rmb, torch, stream, hbm, peak_kind):
         rows.append({"mdp": "maze100 warm start", "b": b, "selection": label + (f" refresh={refresh}" if refresh else ""),
                      "ms": round(min(ts), 3), "sweeps": hi, "err": err()})
     best = next(r for r in rows if r["mdp"] == "csr2e20" and r["b"] == 262144 and r["selection"] == "uniform")
-    # the FP64 oracle on the host cores: uniform-draw sweeps of the same MDP (bounded sample)
-    import oracle
-    Vc = np.zeros(mdp.n)
-    t0 = time.perf_counter()
-    csw = 0
-    while csw < 50 and time.perf_counter() - t0 < 10.0:
-        Vc = oracle.mbvi(mdp, 262144, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=1, V0=Vc, start_sweep=csw,
-                         select=1)["V"]
-        csw += 1
-    ct = time.perf_counter() - t0
+    # CPU-baseline leg: the FP64 oracle on the host cores, uniform-draw sweeps of the same MDP (bounded)
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        Vc = np.zeros(mdp.n)
+        t0 = time.perf_counter()
+        csw = 0
+        while csw < 50 and time.perf_counter() - t0 < 10.0:
+            Vc = oracle.mbvi(mdp, 262144, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=1, V0=Vc, start_sweep=csw,
+                             select=1)["V"]
+            csw += 1
+        ct = time.perf_counter() - t0
+        cpu = {"value": mdp.n * csw / ct, "unit": "Bellman backups/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"{csw} uniform-draw MB-VI sweeps (b=262144) of the n=2^20 MDP "
+                                           f"from V=0, FP64, {ct:.1f} s"}
     ach = best["sweeps"] * sweep_bytes(mdp.n, M_ACTIONS, K_SUCC) / (best["ms"] / 1e3) / 1e9
     return _line("batch selection with replacement: CSR n=2^20 MB-VI to 1e-6 with uniform draws (b=262144)",
                  mdp.n * best["sweeps"] / (best["ms"] / 1e3), "Bellman backups/s", best["ms"], args, world,
@@ -871,9 +924,7 @@ def _select(args, world, rmb, torch, stream, hbm, peak_kind):
                            "traffic": None, "kernel": "rmb_csr_vec_kernel (draws)", "peak_kind": peak_kind,
                            "note": "P stream per sweep x sweeps / solve time; bound by random successor gathers "
                                    "as the sigma solve"},
-                 cpu_baseline={"value": mdp.n * csw / ct, "unit": "Bellman backups/s", "cores": oracle.num_threads(),
-                               "kind": "oracle", "sample": f"{csw} uniform-draw MB-VI sweeps (b=262144) of the "
-                                                           f"n=2^20 MDP from V=0, FP64, {ct:.1f} s"})
+                 cpu_baseline=cpu)
 
 
 if __name__ == "__main__":
