@@ -680,7 +680,8 @@ __device__ __forceinline__ int try_wait_bounded(uint32_t mb, uint32_t parity, lo
     return 1;
 }
 
-__device__ __forceinline__ bool stage_values(const KP& p, DenseSmem& sm, float* dst, const float* src, int nfl)
+// bulk copy of nfl floats into shared memory (issued by thread 0); stage_wait completes it
+__device__ __forceinline__ void stage_issue(DenseSmem& sm, float* dst, const float* src, int nfl)
 {
     // nfl is a multiple of 4 floats (16 bytes), src and dst 16-byte aligned
     const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&sm.mbar);
@@ -692,6 +693,12 @@ __device__ __forceinline__ bool stage_values(const KP& p, DenseSmem& sm, float* 
         asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      ::"r"(d), "l"(src), "r"(bytes), "r"(mb) : "memory");
     }
+}
+
+// every thread of the CTA: wait (bounded) for the copy issued by stage_issue
+__device__ __forceinline__ bool stage_wait(const KP& p, DenseSmem& sm)
+{
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&sm.mbar);
     const uint32_t parity = sm.phase & 1u;
     if (threadIdx.x == 0) {
         // bounded wait; after a timeout wait (bounded again) for the copy in flight to land
@@ -708,6 +715,12 @@ __device__ __forceinline__ bool stage_values(const KP& p, DenseSmem& sm, float* 
     __syncthreads();
     if (threadIdx.x == 0) sm.phase++;
     return ok;
+}
+
+__device__ __forceinline__ bool stage_values(const KP& p, DenseSmem& sm, float* dst, const float* src, int nfl)
+{
+    stage_issue(sm, dst, src, nfl);
+    return stage_wait(p, sm);
 }
 
 // Dense row elements: float32, or bf16 / fp8-e4m3 codes.  Coded rows are renormalised by the sum of
@@ -888,7 +901,8 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
     const int me = gv.rank;
     if (me >= len) return true;
     bool ok = true;
-    if (whole && !stage_values(p, sm, stage, A, (p.n + 3) & ~3)) return false;
+    // the values' bulk copy is in flight while the first block of states resolves
+    if (whole) stage_issue(sm, stage, A, (p.n + 3) & ~3);
     for (int j0 = 0; me + j0 * G < len; j0 += 32) {
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -897,6 +911,7 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
             if (pos < len) st = K ? state_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
             sm.perm[threadIdx.x] = st;
         }
+        if (j0 == 0 && whole && !stage_wait(p, sm)) return false;
         __syncthreads();
         for (int jj = 0; jj < 32; ++jj) {
             const int s = sm.perm[jj];
@@ -2434,6 +2449,9 @@ int solve(const Call& q)
     const int max_grid = per_sm * D->sms;
     int grid = O->grid_ctas > 0 ? O->grid_ctas : max_grid;
     if (grid > max_grid) grid = max_grid;
+    // dense rows take one CTA per state: with batches smaller than the grid, one CTA per SM is enough
+    // (fewer CTAs at every grid barrier, no two sharing an SM)
+    if (O->grid_ctas == 0 && path == PATH_DENSE && b < grid) grid = (int)std::max<int64_t>(b, D->sms);
 
     cudaStream_t s = q.stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
