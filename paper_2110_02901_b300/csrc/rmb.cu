@@ -901,8 +901,7 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
     const int me = gv.rank;
     if (me >= len) return true;
     bool ok = true;
-    // the values' bulk copy is in flight while the first block of states resolves
-    if (whole) stage_issue(sm, stage, A, (p.n + 3) & ~3);
+    if (whole && !stage_values(p, sm, stage, A, (p.n + 3) & ~3)) return false;
     for (int j0 = 0; me + j0 * G < len; j0 += 32) {
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -911,7 +910,6 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
             if (pos < len) st = K ? state_at((uint32_t)(pos0 + pos), *K, perm_ok) : pos0 + pos;
             sm.perm[threadIdx.x] = st;
         }
-        if (j0 == 0 && whole && !stage_wait(p, sm)) return false;
         __syncthreads();
         for (int jj = 0; jj < 32; ++jj) {
             const int s = sm.perm[jj];
@@ -1418,11 +1416,11 @@ struct Runner {
                 c_s = ld_l2(p.S[(t - 1) & 1] + c0);
                 c_v = ld_l2(p.W[(t - 1) & 1] + c0);
             }
-            // stamps are unique within the solve (mark is cleared at set-up)
-            const uint64_t stamp = p.mark ? (uint64_t)(k - p.start_sweep) * (uint64_t)p.T + (uint64_t)t + 1u : 0u;
             if (!batch<KIND>(A, B, t * p.b, len, ordered ? &K : nullptr, ordered ? p.S[t & 1] : nullptr,
                              ordered ? p.W[t & 1] : nullptr, acc))
                 return false;
+            // stamps are unique within the solve (mark is cleared at set-up)
+            const uint64_t stamp = p.mark ? (uint64_t)(k - p.start_sweep) * (uint64_t)p.T + (uint64_t)t + 1u : 0u;
             uint64_t* mk = p.mark ? p.mark + (size_t)(t & 1) * (size_t)p.n : nullptr;
             if (c_s >= 0 && !(stamp && ld_l2(mk + c_s) == stamp)) st_l2(B + c_s, c_v);
             if (t >= 1) copy_batch(p.S[(t - 1) & 1], p.W[(t - 1) & 1], p.b, B, gthreads(), stamp, mk);
