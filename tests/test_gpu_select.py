@@ -190,3 +190,30 @@ def test_prioritized_vi_reaches_the_optimum():
     res = rmb.prioritized_vi(dm, V, batch=64, eps=1e-6, refresh=4, floor_frac=0.05)
     assert res["status"] == rmb.RMB_OK and res["residual"] <= 1e-6
     close(V.cpu().numpy(), jstar)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 37])
+def test_tiny_problems_with_draws_and_stop_tests(n):
+    mdp = mdpgen.csr_ragged(n, 3, 3, gamma=0.9, seed=n)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    w = (np.arange(n, dtype=np.uint32) % 4) + 1
+    V0 = mdpgen.random_values(n, seed=1)
+    for b in sorted({1, 2, n}):
+        b = min(b, n)
+        for select in (1, 2):
+            ref = oracle.mbvi(mdp, b, 3, eps=0.0, max_sweeps=5, V0=V0, select=select, weights=w)
+            V = torch.from_numpy(V0).cuda()
+            rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=3, eps=0.0, max_sweeps=5, select=select,
+                                    weights=dev_w(w) if select == 2 else None), V)
+            close(V.cpu().numpy(), ref["V"])
+        for rk in (0, 1):
+            ref = oracle.mbvi(mdp, b, 3, eps=1e-6, max_sweeps=10000, V0=V0, residual_kind=rk)
+            V = torch.from_numpy(V0).cuda()
+            st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=3, eps=1e-6, max_sweeps=10000, residual_kind=rk), V)
+            assert st["status"] == rmb.RMB_OK
+            close(V.cpu().numpy(), ref["V"], tol=2e-5)
+    jstar, _, _ = exact.policy_iteration(mdp)
+    V = torch.zeros(n, dtype=torch.float32, device="cuda")
+    st = rmb.rmb_vi(dm, rmb.Opts(batch=1, eps=1e-7, max_sweeps=100000, flags=rmb.RMB_FLAG_ASYNC), V)
+    assert st["status"] == rmb.RMB_OK
+    close(V.cpu().numpy(), jstar)
