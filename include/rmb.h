@@ -71,7 +71,9 @@ typedef struct {
     const int64_t *row_ptr;  /* RMB_CSR: [n*m+1] */
     const int32_t *col;      /* RMB_CSR: [nnz] */
     const float *prob;       /* RMB_CSR: [nnz] */
-    const float *cost;       /* [n*m]; +inf = action not admissible */
+    const float *cost;       /* [n*m]; +inf = action not admissible; NaN and -inf are invalid
+                                (rmb_validate rejects them; unvalidated, a NaN cost drops its action
+                                from the minimum like +inf) */
     double gamma;            /* discount, 0 < gamma < 1 */
     int32_t k_uniform;       /* RMB_CSR: k > 0 declares row_ptr[r] == r*k for every row (enables
                                 the vectorised row path; checked when validate != 0); 0 = unknown */

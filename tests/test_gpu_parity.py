@@ -359,3 +359,24 @@ def test_bellman_residual_stop_test_matches_oracle():
             assert float(np.abs(exact.bellman_pass(mdp, v)[0] - v).max()) <= 1.2e-5
             assert abs(st["sweeps"] - ref["sweeps"]) <= 2
             assert np.abs(v - ref["V"]).max() <= 1e-4 * max(1.0, np.abs(ref["V"]).max())
+
+
+def test_nonfinite_inputs_are_reported():
+    """A NaN start value ends the solve with RMB_ERR_NONFINITE and a NaN cost is rejected by the
+    validation pass (statuses, not faults); the library keeps working afterwards."""
+    mdp = mdpgen.csr_uniform_k(2000, 4, 8, gamma=0.9, seed=2)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    V0 = mdpgen.random_values(mdp.n, seed=1)
+    V0[17] = np.nan
+    V = torch.from_numpy(V0).cuda()
+    st, _ = rmb.rmb_vi(dm, rmb.Opts(batch=100, eps=1e-6, max_sweeps=50), V, check=False)
+    assert st == rmb.RMB_ERR_NONFINITE
+    bad = mdpgen.csr_uniform_k(2000, 4, 8, gamma=0.9, seed=2)
+    bad.cost = bad.cost.copy()
+    bad.cost[4 * 33] = np.nan
+    dbad = rmb.DeviceMDP.from_host(bad)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    st, _ = rmb.rmb_vi(dbad, rmb.Opts(batch=100, eps=1e-6, max_sweeps=50, validate=True), V, check=False)
+    assert st == rmb.RMB_ERR_INVALID_MDP
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    assert rmb.rmb_vi(dm, rmb.Opts(batch=100, eps=1e-6), V)["status"] == rmb.RMB_OK
