@@ -1,0 +1,66 @@
+// librmb: the persistent CSR kernels (vectorised rows, ragged rows) and the batched kernel, which
+// runs the same CSR runners (a translation unit of its own so that the library compiles in parallel).
+
+#include "rmb_core.cuh"
+
+namespace rmb {
+
+// CSR rows with k % 4 == 0: NCA / NCO = float4 chunks per lane in the min-over-actions sweeps and in
+// the policy-row sweeps (0 = the general row loop).
+template <int NCA, int NCO>
+__global__ void __launch_bounds__(kCsrThreads, 1) rmb_csr_vec_kernel(KP p)
+{
+    __shared__ RedSmem rs;
+    Runner<PATH_CSR_VEC, NCA, NCO> R(p, rs, nullptr, nullptr, GroupView{(int)blockIdx.x, (int)gridDim.x});
+    R.run();
+}
+
+__global__ void __launch_bounds__(kCsrThreads, 1) rmb_csr_gen_kernel(KP p)
+{
+    __shared__ RedSmem rs;
+    Runner<PATH_CSR_GEN> R(p, rs, nullptr, nullptr, GroupView{(int)blockIdx.x, (int)gridDim.x});
+    R.run();
+}
+
+
+const void* csr_vec_kernel_for(int nca, int nco)
+{
+    const int a = (nca == 1 || nca == 2 || nca == 4) ? nca : 0;
+    const int o = nco == 1 ? 1 : 0;
+#define RMB_K(A_, O_) if (a == A_ && o == O_) return reinterpret_cast<const void*>(rmb_csr_vec_kernel<A_, O_>);
+    RMB_K(0, 0) RMB_K(1, 0) RMB_K(2, 0) RMB_K(4, 0) RMB_K(0, 1) RMB_K(1, 1) RMB_K(2, 1) RMB_K(4, 1)
+#undef RMB_K
+    return reinterpret_cast<const void*>(rmb_csr_vec_kernel<0, 0>);
+}
+
+const void* csr_gen_kernel_ptr() { return reinterpret_cast<const void*>(rmb_csr_gen_kernel); }
+
+__global__ void __launch_bounds__(kCsrThreads, 1)
+rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off, const BatchTask* __restrict__ tasks)
+{
+    __shared__ RedSmem rs;
+    __shared__ KP s_kp;
+    const int t0 = task_off[blockIdx.x], t1 = task_off[blockIdx.x + 1];
+    for (int t = t0; t < t1; ++t) {
+        const BatchTask bt = tasks[t];
+        __syncthreads();
+        if (threadIdx.x == 0) s_kp = kps[bt.item];
+        __syncthreads();
+        const GroupView gv{bt.rank, bt.size};
+        if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 1 && s_kp.nc_one == 1) {
+            Runner<PATH_CSR_VEC, 1, 1> R(s_kp, rs, nullptr, nullptr, gv);
+            R.run();
+        } else if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 2 && s_kp.nc_one == 1) {
+            Runner<PATH_CSR_VEC, 2, 1> R(s_kp, rs, nullptr, nullptr, gv);
+            R.run();
+        } else {
+            Runner<PATH_CSR_GEN> R(s_kp, rs, nullptr, nullptr, gv);
+            R.run();
+        }
+    }
+}
+
+
+const void* batched_kernel_ptr() { return reinterpret_cast<const void*>(rmb_batched_kernel); }
+
+}  // namespace rmb
