@@ -35,7 +35,7 @@ import mdpgen  # noqa: E402
 METRIC = "time-to-1e-6 residual and Bellman backups/s vs batch b; P-stream HBM GB/s"
 N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
-CSR_DRAM_BYTES_PER_STATE_PASS = (11167743488 + 10897408) / (21 * 262144)
+CSR_DRAM_BYTES_PER_STATE_PASS = (11168375296 + 11002624) / (21 * 262144)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]
 HEADLINE_B = 262144
 MPI_K = 10
