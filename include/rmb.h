@@ -172,7 +172,10 @@ size_t rmb_workspace_bytes(const rmb_mdp *mdp, const rmb_opts *opts);
  * sigma_{seed,k} (Sec. III-A, Sec. IV-A) and updates them in batches of b positions: every
  * state of batch t reads the new values of batches < t and the old values of the rest (its own
  * batch included), so b = 1 is Gauss-Seidel and b = n is the Bellman operator T.
- * Stops after the first sweep whose sup-norm change is <= eps, or after max_sweeps sweeps.
+ * Stops after the first sweep whose sup-norm change is <= eps (confirmed by ||TV - V||_inf <= eps
+ * with residual_kind = RMB_RESIDUAL_BELLMAN or with draws), or after max_sweeps sweeps.  Options:
+ * opts.flags = RMB_FLAG_ASYNC (asynchronous sweeps, CSR), opts.select / opts.weights (batches drawn
+ * with replacement).
  *   V_inout  [n] float32: start values on entry (the paper uses 0), final values on exit.
  *   pi_out   [n] int32 or NULL: greedy policy at the final values (lowest action on ties).
  *   qgap_out [n] float32 or NULL: second smallest minus smallest Q-factor at the final values.
