@@ -694,6 +694,10 @@ def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
         step()
     ms, outs = _timed(step, args.steps, stream)
     st1, st2 = outs[-1]
+    nk = mdp.n * mdp.uniform_k()
+    fwd_bytes = (st1["sweeps"] + 1) * (mdp.nnz * 8 + mdp.n * mdp.m * 4)
+    adj_bytes = st2["sweeps"] * (nk * 8 + mdp.n * 8) + nk * 8
+    ach = (fwd_bytes + adj_bytes) / ((st1["ms"] + st2["ms"]) / 1e3) / 1e9
     cpu = None
     if not args.no_cpu:   # CPU-baseline leg: the FP64 direct-solve gradient on the host
         from oracle import exact
@@ -708,7 +712,14 @@ def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
                               "b=4096 to 1e-7, adjoint mini-batch sweeps b=4096 to 1e-7",
                   "forward_ms": st1["ms"], "forward_sweeps": st1["sweeps"], "adjoint_ms": st2["ms"],
                   "adjoint_sweeps": st2["sweeps"]},
-                 roofline=None, cpu_baseline=cpu)
+                 roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                           "traffic": None, "kernel": "rmb_csr_vec_kernel (forward) + rmb_csr_gen_kernel (adjoint)",
+                           "peak_kind": peak_kind,
+                           "note": "algorithmic bytes: forward (sweeps + 1) x (nnz x 8 + n m 4), adjoint sweeps x "
+                                   "(n k 8 + n 8), gradient pass n k 8, over the two solves' device time; P (67 MB) "
+                                   "fits in the 126 MB L2 and a batch of 4096 states costs ~6 us of barrier and "
+                                   "dependent-load latency, so the solves are latency-bound"},
+                 cpu_baseline=cpu)
 
 
 # speed-ups at 1e-4 of J* printed in Sec. IV-B (GTX 1650 Ti): context, not targets
