@@ -679,8 +679,10 @@ def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
     w = torch.from_numpy(mdpgen.random_values(mdp.n, seed=13)).cuda()
     V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
     pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
-    fo = rmb.Opts(batch=4096, seed=mdpgen.PERM_SEED, eps=1e-7, max_sweeps=100000, validate=False)
-    go = rmb.Opts(batch=4096, seed=5, eps=1e-7, max_sweeps=100000)
+    # b = 16384: at n = 65536 the solves are latency-bound, and 4 batches per sweep beat 16 (b = 4096:
+    # 38 ms per gradient, b = 16384: 24 ms, b = 65536: 24 ms)
+    fo = rmb.Opts(batch=16384, seed=mdpgen.PERM_SEED, eps=1e-7, max_sweeps=100000, validate=False)
+    go = rmb.Opts(batch=16384, seed=5, eps=1e-7, max_sweeps=100000)
     fws = rmb.workspace(dm, fo)
 
     def step():
@@ -704,12 +706,12 @@ def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
         t0 = time.perf_counter()
         exact.fixed_point_gradient(mdp, w.cpu().numpy().astype(np.float64))
         ct = time.perf_counter() - t0
-        cpu = {"value": 1.0 / ct, "unit": "gradients/s", "cores": 0, "kind": "oracle",
+        cpu = {"value": 1.0 / ct, "unit": "gradients/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
                "sample": f"direct-solve gradient (policy iteration + GMRES adjoint), {ct:.1f} s"}
     return _line("time of forward solve + adjoint gradient (w.V*, dcost and dlogits)", 1e3 / ms, "gradients/s", ms,
                  args, world,
                  {"workload": "csr-mdp n=65536 m=8 k=16 P=softmax(N(0,1) logits) c~U[0,1] gamma=0.95; forward MB-VI "
-                              "b=4096 to 1e-7, adjoint mini-batch sweeps b=4096 to 1e-7",
+                              "b=16384 to 1e-7, adjoint mini-batch sweeps b=16384 to 1e-7",
                   "forward_ms": st1["ms"], "forward_sweeps": st1["sweeps"], "adjoint_ms": st2["ms"],
                   "adjoint_sweeps": st2["sweeps"]},
                  roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
@@ -717,8 +719,8 @@ def _adjoint(args, world, rmb, torch, stream, hbm, peak_kind):
                            "peak_kind": peak_kind,
                            "note": "algorithmic bytes: forward (sweeps + 1) x (nnz x 8 + n m 4), adjoint sweeps x "
                                    "(n k 8 + n 8), gradient pass n k 8, over the two solves' device time; P (67 MB) "
-                                   "fits in the 126 MB L2 and a batch of 4096 states costs ~6 us of barrier and "
-                                   "dependent-load latency, so the solves are latency-bound"},
+                                   "fits in the 126 MB L2 and each batch costs barrier and dependent-load latency, so "
+                                   "the solves are latency-bound"},
                  cpu_baseline=cpu)
 
 
