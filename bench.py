@@ -361,10 +361,12 @@ def main():
     # b-sweep side table (one warm + one timed solve per entry, outside the headline timing)
     bsweep = []
     if not args.no_sweep and rank == 0:
-        for bb in B_SWEEP + ["async"]:
-            # "async": asynchronous sweeps (no barrier between batches, in-place writes)
+        for bb in B_SWEEP + ["auto", "async"]:
+            # "auto": b chosen by the library's time model (opts.batch = 0); "async": asynchronous
+            # sweeps (no barrier between batches, in-place writes)
+            label = bb
             flags = rmb.RMB_FLAG_ASYNC if bb == "async" else 0
-            bb = n if bb == "async" else min(bb, n)
+            bb = n if bb == "async" else (0 if bb == "auto" else min(bb, n))
             for scheme in ("vi", "mpi"):
                 o = rmb.Opts(batch=bb, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=200000 if scheme == "vi" else 20000,
                              eval_sweeps=MPI_K, validate=False, flags=flags)
@@ -378,7 +380,8 @@ def main():
                         res = rmb.rmb_mpi(dm, o, V, pi, gap, ws=w, stream=stream)
                 passes = (res["sweeps"] + 1) if scheme == "vi" else (res["iters"] + res["sweeps"] / M_ACTIONS)
                 gbs = passes * sweep_bytes(n, M_ACTIONS, K_SUCC) / (res["ms"] / 1e3) / 1e9
-                bsweep.append({"b": "async" if flags else bb, "scheme": scheme, "time_to_eps_ms": res["ms"], "sweeps": res["sweeps"],
+                bsweep.append({"b": label if isinstance(label, str) else bb, "b_used": res["batch"], "scheme": scheme,
+                               "time_to_eps_ms": res["ms"], "sweeps": res["sweeps"],
                                "improvements": res["iters"], "backups_per_s": n * res["sweeps"] / (res["ms"] / 1e3),
                                "p_stream_gbs": gbs, "hbm_frac": gbs / hbm, "residual": res["residual"],
                                "barriers": res["barriers"]})

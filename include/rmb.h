@@ -84,7 +84,8 @@ typedef struct {
 
 /* Options of a solve. */
 typedef struct {
-    int64_t batch;           /* mini-batch size b (the paper's m), 1 <= b; b >= n means b = n */
+    int64_t batch;           /* mini-batch size b (the paper's m), 1 <= b; b >= n means b = n;
+                                0 = chosen by the library's time model (stats->batch reports it) */
     uint64_t seed;           /* key of the per-sweep state permutation */
     double eps;              /* stop when the residual <= eps (VI / evaluation: sup-norm change of a
                                 sweep; MPI: ||TV - V||_inf of the improvement pass) */
@@ -160,8 +161,19 @@ typedef struct {
     int32_t path;            /* 0 dense, 1 CSR vectorised rows, 2 CSR generic rows, 3 dense TMA pipeline */
     int32_t lanes_per_state; /* CSR paths: lanes that share one state */
     float ms;                /* device time of the call (CUDA events on `stream`) */
-    int32_t reserved;
+    int32_t batch;           /* the mini-batch size b used (the model's choice when opts.batch = 0) */
 } rmb_stats;
+
+/*
+ * opts.batch = 0: b from a model of one solve on a B300 whose constants come from the measured bench
+ * workloads.  time(b) = sweeps(b) * ceil(n/b) * (max(stream time of one batch, waves of concurrent
+ * states) + 6 us per batch), where sweeps(b) shrinks with b as fitted on the 2^20-state CSR MDP
+ * (the comparison theorem of Sec. III-B.2 says smaller b never needs more sweeps).  CSR: one batch
+ * gathers b * m * k successors at 244 G/s (k = 4 when rows are ragged), 2368 states at once, 1 us per
+ * wave.  Dense: b * m * n element bytes at 6.5 TB/s, 148 states at once, m * n element bytes per
+ * state at 44 GB/s per SM.  b runs over n, n/2, n/4, ..., >= 32.  The choice depends only on the MDP's
+ * sizes, format, gamma and eps, so rmb_workspace_bytes and the solve agree.
+ */
 
 /* Bytes of workspace a call with this MDP and these options needs (0 on invalid arguments). */
 size_t rmb_workspace_bytes(const rmb_mdp *mdp, const rmb_opts *opts);

@@ -69,11 +69,11 @@ class rmb_stats(ctypes.Structure):
         ("sweeps", ctypes.c_int64), ("iters", ctypes.c_int64), ("barriers", ctypes.c_int64),
         ("residual", ctypes.c_double), ("v_shift", ctypes.c_double), ("status", ctypes.c_int32),
         ("grid_ctas", ctypes.c_int32), ("path", ctypes.c_int32), ("lanes_per_state", ctypes.c_int32),
-        ("ms", ctypes.c_float), ("reserved", ctypes.c_int32),
+        ("ms", ctypes.c_float), ("batch", ctypes.c_int32),
     ]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
         d["path"] = PATH_NAMES.get(d["path"], d["path"])
         d["status_text"] = rmb_status_string(d["status"])
         return d

@@ -487,10 +487,13 @@ int check_mdp(const rmb_mdp* M)
     return RMB_OK;
 }
 
+int64_t auto_batch(const rmb_mdp* M, double eps);
+
+// opts.batch: b in [1, n] (larger means n), or 0 for the time model's choice
 int effective_batch(const rmb_mdp* M, const rmb_opts* O, int64_t* b)
 {
-    if (!O || O->batch < 1) return RMB_ERR_ARG;
-    *b = O->batch > M->n ? M->n : O->batch;
+    if (!O || O->batch < 0) return RMB_ERR_ARG;
+    *b = O->batch == 0 ? auto_batch(M, O->eps) : (O->batch > M->n ? M->n : O->batch);
     return RMB_OK;
 }
 
@@ -776,6 +779,7 @@ int solve(const Call& q)
     q.stats->path = path;
     q.stats->lanes_per_state = path == PATH_DENSE ? threads : p.lps_all;
     q.stats->ms = ms;
+    q.stats->batch = (int32_t)b;
     return q.stats->status;
 }
 
@@ -844,6 +848,42 @@ struct ItemPlan {
     int G;
     double t;
 };
+
+// The single-solve time model of opts.batch = 0 (constants measured on this library's bench workloads on
+// a B300: the random-gather rate of the CSR kernel, the dense TMA stream rate, the per-batch barrier
+// and epilogue latency); sweeps(b) is est_sweeps' factor.  Independent of the device and of the mode,
+// so the workspace size and the solve always agree on b.
+int64_t auto_batch(const rmb_mdp* M, double eps)
+{
+    const double n = (double)M->n;
+    double per_state_us, conc, wave_us;
+    if (M->format == RMB_CSR) {
+        const double k = M->k_uniform > 0 ? (double)M->k_uniform : 4.0;
+        per_state_us = (double)M->m * k / 244.0e3;          // 244 G random gathers/s over the grid
+        conc = 148.0 * 16.0;
+        wave_us = 1.0;
+    } else {
+        const double eb = M->p_dtype == RMB_P_F32 ? 4.0 : (M->p_dtype == RMB_P_BF16 ? 2.0 : 1.0);
+        per_state_us = (double)M->m * n * eb / 6.5e6;        // 6.5 TB/s over the grid
+        conc = 148.0;
+        wave_us = (double)M->m * n * eb / 44.0e3;            // 44 GB/s per SM
+    }
+    const double gamma = M->gamma;
+    int64_t best = M->n;
+    double best_t = 1e300;
+    for (int64_t b = M->n;; b = (b + 1) / 2) {
+        const double T = std::ceil(n / (double)b);
+        const double stream = (double)b * per_state_us;
+        const double waves = std::ceil((double)b / conc) * wave_us;
+        const double t = est_sweeps(gamma, eps, (double)b / n) * T * ((stream > waves ? stream : waves) + 6.0);
+        if (t < best_t * (1.0 - 1e-9)) {   // ties keep the larger b
+            best_t = t;
+            best = b;
+        }
+        if (b <= 32) break;
+    }
+    return best;
+}
 
 ItemPlan best_b(const ItemCost& c, int G, double eps, int64_t fixed_b)
 {
@@ -1194,6 +1234,7 @@ size_t rmb_workspace_bytes(const rmb_mdp* mdp, const rmb_opts* opts)
     if (check_mdp(mdp)) return 0;
     int64_t b = mdp->n;
     if (opts && opts->batch >= 1) b = opts->batch > mdp->n ? mdp->n : opts->batch;
+    if (opts && opts->batch == 0) b = auto_batch(mdp, opts->eps);
     return layout(mdp->n, b, opts ? opts->select : RMB_SELECT_PERMUTATION).total;
 }
 

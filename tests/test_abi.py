@@ -90,7 +90,7 @@ def _opts(b=10, max_sweeps=10, eps=1e-6):
     return rmb.Opts(batch=b, max_sweeps=max_sweeps, eps=eps).desc()
 
 
-@pytest.mark.parametrize("bad", ["null_mdp", "n0", "m0", "gamma1", "gamma0", "fmt", "b0", "sweeps0", "eps_neg",
+@pytest.mark.parametrize("bad", ["null_mdp", "n0", "m0", "gamma1", "gamma0", "fmt", "b_neg", "sweeps0", "eps_neg",
                                  "eps_nan", "no_v", "ws_null", "ws_misaligned", "ws_small", "n_huge", "no_cost"])
 def test_argument_errors_need_no_gpu(L, bad):
     d, o = _fake_mdp(), _opts()
@@ -108,8 +108,8 @@ def test_argument_errors_need_no_gpu(L, bad):
         d.gamma = 0.0
     elif bad == "fmt":
         d.format = 7
-    elif bad == "b0":
-        o.batch = 0
+    elif bad == "b_neg":
+        o.batch = -1
     elif bad == "sweeps0":
         o.max_sweeps = 0
     elif bad == "eps_neg":

@@ -380,3 +380,22 @@ def test_nonfinite_inputs_are_reported():
     assert st == rmb.RMB_ERR_INVALID_MDP
     V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
     assert rmb.rmb_vi(dm, rmb.Opts(batch=100, eps=1e-6), V)["status"] == rmb.RMB_OK
+
+
+@pytest.mark.parametrize("make", [lambda: mdpgen.csr_uniform_k(20000, 8, 32, gamma=0.95, seed=8),
+                                  lambda: mdpgen.csr_ragged(3000, 4, 9, gamma=0.9, seed=9),
+                                  lambda: mdpgen.dense_dirichlet(700, 4, gamma=0.95, seed=10)])
+def test_batch_zero_uses_the_time_model_choice(make):
+    """opts.batch = 0: the library picks b (reported in stats['batch']); the solve equals the oracle
+    at that b, and the workspace sized for batch = 0 is the one the solve needs."""
+    mdp = make()
+    dm = rmb.DeviceMDP.from_host(mdp)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    st = rmb.rmb_vi(dm, rmb.Opts(batch=0, seed=4, eps=0.0, max_sweeps=6), V)
+    b = st["batch"]
+    assert 1 <= b <= mdp.n and st["sweeps"] == 6
+    ref = oracle.mbvi(mdp, b, 4, eps=0.0, max_sweeps=6)
+    close(V.cpu().numpy(), ref["V"])
+    V2 = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    st2 = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=4, eps=0.0, max_sweeps=6), V2)
+    assert st2["batch"] == b and torch.equal(V, V2)
