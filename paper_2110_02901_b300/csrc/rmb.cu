@@ -1456,6 +1456,9 @@ int rmb_vi_refined(const rmb_mdp* lowp, const rmb_mdp* ref, const rmb_opts* opts
     if (lowp->n != ref->n || lowp->m != ref->m || lowp->gamma != ref->gamma || lowp->cost != ref->cost)
         return RMB_ERR_ARG;
     rmb_opts o1 = *opts;
+    // batch = 0: one b for both solves, the model's choice for the reference rows (the workspace is
+    // sized by rmb_workspace_bytes(ref, opts))
+    if (opts->batch == 0) o1.batch = auto_batch(ref, opts->eps);
     o1.eps = eps_low;
     o1.trace = nullptr;
     Call q1{MODE_VI, lowp, &o1, V_inout, V_inout, nullptr, nullptr, nullptr, nullptr,
@@ -1463,6 +1466,7 @@ int rmb_vi_refined(const rmb_mdp* lowp, const rmb_mdp* ref, const rmb_opts* opts
     st = solve(q1);
     if (st != RMB_OK && st != RMB_ERR_NOT_CONVERGED) return st;
     rmb_opts o2 = *opts;
+    o2.batch = o1.batch;
     o2.trace = nullptr;
     Call q2{MODE_VI, ref, &o2, V_inout, V_inout, nullptr, pi_out, qgap_out, nullptr,
             workspace, workspace_bytes, stats_ref, static_cast<cudaStream_t>(stream)};

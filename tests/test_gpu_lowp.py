@@ -127,3 +127,17 @@ def test_converged_lowp_and_refined_solutions(dt):
     print(f"dtype={dt}: relative error vs float32 problem, low precision {lowp_err:.2e}, refined {ref_err:.2e}, "
           f"sweeps {s1['sweeps']} + {s2['sweeps']}")
     assert ref_err < lowp_err
+
+
+def test_refined_solve_with_model_batch():
+    """batch = 0 in rmb_vi_refined: one b (the model's, for the float32 rows) for both solves, in the
+    workspace sized for the float32 MDP."""
+    n = 2048
+    mdp = mdpgen.dense_dirichlet(n, 8, alpha=0.1, gamma=0.99, seed=7, cost_dist="normal")
+    dm = rmb.DeviceMDP.from_host(mdp)
+    lp = rmb.dense_lowp(dm, rmb.RMB_P_FP8E4M3)
+    V = torch.zeros(n, dtype=torch.float32, device="cuda")
+    s1, s2 = rmb.rmb_vi_refined(lp, dm, rmb.Opts(batch=0, seed=5, eps=1e-6, max_sweeps=100000), 1e-6, V)
+    assert s2["status"] == rmb.RMB_OK and s1["batch"] == s2["batch"] >= 1
+    ref = oracle.mbvi(mdp, s2["batch"], seed=5, eps=1e-7, max_sweeps=100000)
+    close(V.cpu().numpy(), ref["V"], tol=2e-5)
