@@ -305,7 +305,7 @@ size_t rmb_fixed_point_grad_workspace_bytes(const rmb_mdp *mdp, const rmb_opts *
  * and
  *   dL/dcost(s,a)    = lambda(s) [a = pi(s)],
  *   dL/dlogit(s,a,t) = gamma lambda(s) [a = pi(s)] p_t (V*(j_t) - sum_u p_u V*(j_u)).
- * lambda is computed by mini-batch sweeps (b = opts.batch, the permutation of opts.seed) of
+ * lambda is computed by mini-batch sweeps (b = opts.batch >= 1, the permutation of opts.seed) of
  * lambda <- w + gamma P_pi^T lambda on the transposed greedy chain, built on the device (rows sorted
  * by predecessor, so the result is deterministic), starting from lambda = w, until the sup-norm
  * change of a sweep is <= opts.eps or opts.max_sweeps.  RMB_CSR with k_uniform > 0 only.
