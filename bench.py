@@ -36,7 +36,7 @@ METRIC = "time-to-1e-6 residual and Bellman backups/s vs batch b; P-stream HBM G
 N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
 CSR_DRAM_BYTES_PER_STATE_PASS = (11168375296 + 11002624) / (21 * 262144)
-DENSE_DRAM_BYTES_PER_P_BYTE = (4285074176 + 4448512) / (4 * 4096 * 16 * 4096 * 4)
+DENSE_DRAM_BYTES_PER_P_BYTE = (4285128192 + 3765760) / (4 * 4096 * 16 * 4096 * 4)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]
 HEADLINE_B = 262144
 MPI_K = 10
@@ -591,7 +591,7 @@ def _dense16k(args, world, rmb, torch, stream, hbm, peak_kind):
                  roofline={"bound": "hbm", "achieved": best["p_stream_gbs"], "peak": hbm, "unit": "GB/s",
                            "frac": best["p_stream_gbs"] / hbm,
                            # 20 sweeps of P per launch x DRAM bytes per P byte of one ncu capture of this
-                           # kernel (n = 4096, 4 sweeps: 4.2895 GB for 4.2950 GB of P)
+                           # kernel (n = 4096, 4 sweeps: 4.2889 GB for 4.2950 GB of P)
                            "traffic": 20 * n * m * n * 4 * DENSE_DRAM_BYTES_PER_P_BYTE,
                            "traffic_note": "ncu capture at n=4096 scaled by P bytes",
                            "kernel": "rmb_dense_tma_kernel<f32>", "peak_kind": peak_kind},

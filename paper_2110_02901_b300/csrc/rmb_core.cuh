@@ -937,8 +937,8 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
 // ------------------------------------------------------------------------------------------------
 constexpr int kTmaConsumers = 8;                    // consumer warps
 constexpr int kTmaThreads = (kTmaConsumers + 1) * 32;
-constexpr int kRingStages = 4;
-constexpr int kStageBytes = 32768;
+constexpr int kRingStages = 2;
+constexpr int kStageBytes = 65536;
 constexpr int kTmaRowGroup = 8;                     // rows per stage (all-action passes)
 constexpr int kTmaMaxStates = 512;                  // states per chunk of a batch
 
@@ -1089,6 +1089,7 @@ __device__ bool dense_batch_tma(const KP& p, const GroupView& gv, TmaSmem& sm, f
                             const int width = min(TC, n - t * TC);
                             const unsigned char* st = ring + (size_t)slot * kStageBytes;
                             const float* vt = vst + (size_t)t * TC;
+#pragma unroll 2
                             for (int jv = tid; jv < width / E; jv += kTmaConsumers * 32) {
                                 float v[E];
 #pragma unroll
