@@ -739,6 +739,15 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
     measure of Sec. IV-B.  J* comes from a GPU MB-MPI solve to ||TV - V||_inf <= 1e-7 (error below
     1.9e-6 by the contraction bound).  The sweep count k*(b) is found by stepping one sweep (MPI: one
     improvement round) at a time; the timed run is a fresh solve from 0 capped at k*(b)."""
+    if args.profile_case:
+        # profiling mode: one MB-VI solve of exactly profile_case sweeps on the N = 100 maze at b = 512
+        mdp = mdpgen.maze100()
+        dm = rmb.DeviceMDP.from_host(mdp)
+        V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=512, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=args.profile_case,
+                                     validate=False), V)
+        return {"profile_case": True, "n": mdp.n, "b": 512, "sweeps": st["sweeps"], "ms": st["ms"],
+                "barriers": st["barriers"], "us_per_batch": 1e3 * st["ms"] / st["barriers"], "path": st["path"]}
     TOL = 1e-4
     K = 50
     rows, lines = [], {}
