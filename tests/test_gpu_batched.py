@@ -102,3 +102,21 @@ def test_batched_fixed_batch_sizes_are_respected():
         assert res[i]["sweeps"] == 5
         v = Vs[i].cpu().numpy().astype(np.float64)
         assert np.max(np.abs(v - ref["V"])) <= 1e-5 * max(1.0, np.abs(ref["V"]).max())
+
+
+def test_batched_full_config_sampled_against_oracle():
+    """The bench's batched workload at full size (256 MDPs, n log-uniform in [256, 65536], m in 2..16,
+    k = 16) in one launch with the autotuned plan; every MDP converges, and 8 sampled MDPs equal the
+    FP64 oracle's MB-VI at their planned b."""
+    mdps = mdpgen.config3()
+    opts = rmb.Opts(batch=1, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000)
+    dms, Vs, pis, B = _run_batch(mdps, opts)
+    B.run()
+    res = B.results()
+    plan = B.plan_table()
+    assert all(r["status"] == rmb.RMB_OK for r in res)
+    rng = np.random.default_rng(5)
+    for i in sorted(rng.choice(len(mdps), size=8, replace=False)):
+        ref = oracle.mbvi(mdps[i], plan[i]["batch"], seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000)
+        v = Vs[i].cpu().numpy().astype(np.float64)
+        assert np.max(np.abs(v - ref["V"])) <= 1e-5 * max(1.0, np.abs(ref["V"]).max()), i
