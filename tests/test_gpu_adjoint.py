@@ -139,8 +139,8 @@ def test_autograd_function_and_full_size_config():
     dm = rmb.DeviceMDP.from_host(mdp)
     cost = torch.from_numpy(mdp.cost).cuda().requires_grad_(True)
     logits = torch.from_numpy(mdp.logits).cuda().requires_grad_(True)
-    opts = rmb.Opts(batch=4096, seed=12345, eps=1e-7, max_sweeps=100000)
-    V, pi = fixed_point(cost, logits, dm, opts, rmb.Opts(batch=4096, seed=5, eps=1e-7, max_sweeps=100000))
+    opts = rmb.Opts(batch=16384, seed=12345, eps=1e-7, max_sweeps=100000)     # the bench's launch configuration
+    V, pi = fixed_point(cost, logits, dm, opts, rmb.Opts(batch=16384, seed=5, eps=1e-7, max_sweeps=100000))
     w = mdpgen.random_values(mdp.n, seed=13).astype(np.float64)
     loss = (torch.from_numpy(w.astype(np.float32)).cuda() * V).sum()
     gcost, glog = torch.autograd.grad(loss, [cost, logits])
