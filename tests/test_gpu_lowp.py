@@ -141,3 +141,53 @@ def test_refined_solve_with_model_batch():
     assert s2["status"] == rmb.RMB_OK and s1["batch"] == s2["batch"] >= 1
     ref = oracle.mbvi(mdp, s2["batch"], seed=5, eps=1e-7, max_sweeps=100000)
     close(V.cpu().numpy(), ref["V"], tol=2e-5)
+
+
+def _rows_only_mdp(n, m, gamma, s, rows, cost_s):
+    """A CSR MDP in the oracle's layout that holds state s's m dense rows (all n successors) and a
+    self-loop everywhere else: enough for the oracle to evaluate Q(s, a, J) on the full-size problem."""
+    lens = np.ones(n * m, dtype=np.int64)
+    lens[s * m:(s + 1) * m] = n
+    row_ptr = np.zeros(n * m + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    col = np.repeat(np.arange(n, dtype=np.int32), m)          # self-loops (row r = t*m + a -> state t)
+    prob = np.ones(n * m, dtype=np.float32)
+    col = list(np.split(col, np.arange(1, n * m)))
+    prob = list(np.split(prob, np.arange(1, n * m)))
+    for a in range(m):
+        col[s * m + a] = np.arange(n, dtype=np.int32)
+        prob[s * m + a] = rows[a].astype(np.float32)
+    cost = np.zeros(n * m, dtype=np.float32)
+    cost[s * m:(s + 1) * m] = cost_s
+    return mdpgen.MDP(n=n, m=m, gamma=gamma, fmt="csr", cost=cost, row_ptr=row_ptr,
+                      col=np.concatenate(col), prob=np.concatenate(prob))
+
+
+@pytest.mark.parametrize("dt", [None, rmb.RMB_P_FP8E4M3])
+def test_dense_config4_full_size_sampled(dt):
+    """The dense workload at full size (n = 16384, m = 16, Dirichlet(0.1), gamma = 0.999, P drawn on the
+    device) in the bench's launch configuration (b = 4096): one sweep from random values.  Every state of
+    the first batch reads only the start values, so its new value is min_a Q(s, a, V0); for sampled
+    states the FP64 oracle evaluates Q on the state's rows (float32 rows, or the fp8 codes of the same
+    rows converted on the CPU by torch and renormalised)."""
+    n, m, b, g = 16384, 16, 4096, 0.999
+    P, cost = mdpgen.dense_dirichlet_device(n, m, 0.1, g, seed=3)
+    d32 = rmb.DeviceMDP(n, m, g, "dense", cost, P=P.reshape(-1))
+    dm = d32 if dt is None else rmb.dense_lowp(d32, dt)
+    V0 = mdpgen.random_values(n, seed=4)
+    V = torch.from_numpy(V0).cuda()
+    st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=77, eps=0.0, max_sweeps=1, validate=False), V)
+    assert st["path"] == "dense-tma"
+    v1 = V.cpu().numpy().astype(np.float64)
+    sample = np.random.default_rng(1).choice(oracle.perm(n, 77, 0)[:b], size=4, replace=False)
+    rows = P[torch.from_numpy(sample).cuda()].cpu().numpy()
+    costs = cost.cpu().numpy().reshape(n, m)
+    for i, s in enumerate(sample):
+        R = rows[i]
+        if dt is not None:
+            codes, _ = cpu_codes(R, dt)
+            d = codes.to(torch.float64).numpy()
+            R = d / d.sum(axis=1, keepdims=True)
+        mdp = _rows_only_mdp(n, m, g, int(s), R, costs[s])
+        want = min(oracle.q_factor(mdp, int(s), a, V0.astype(np.float64)) for a in range(m))
+        assert abs(v1[s] - want) <= 1e-5 * max(1.0, abs(want)), (s, v1[s], want)
