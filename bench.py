@@ -229,6 +229,8 @@ def main():
     ap.add_argument("--full", action="store_true", help="dense16k: also time full gamma=0.999 solves at n=16384")
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "fp8"],
                     help="dense16k --profile-case: storage type of P")
+    ap.add_argument("--profile-batch", default="512",
+                    help="maze --profile-case: the batch size, 'n' (one batch) or 'async' (asynchronous sweeps)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -740,13 +742,16 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
     1.9e-6 by the contraction bound).  The sweep count k*(b) is found by stepping one sweep (MPI: one
     improvement round) at a time; the timed run is a fresh solve from 0 capped at k*(b)."""
     if args.profile_case:
-        # profiling mode: one MB-VI solve of exactly profile_case sweeps on the N = 100 maze at b = 512
+        # profiling mode: one MB-VI solve of exactly profile_case sweeps on the N = 100 maze at
+        # b = --profile-batch (default 512)
         mdp = mdpgen.maze100()
         dm = rmb.DeviceMDP.from_host(mdp)
         V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
-        st = rmb.rmb_vi(dm, rmb.Opts(batch=512, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=args.profile_case,
-                                     validate=False), V)
-        return {"profile_case": True, "n": mdp.n, "b": 512, "sweeps": st["sweeps"], "ms": st["ms"],
+        pb = args.profile_batch
+        b = mdp.n if pb in ("n", "async") else int(pb)
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=args.profile_case,
+                                     validate=False, flags=rmb.RMB_FLAG_ASYNC if pb == "async" else 0), V)
+        return {"profile_case": True, "n": mdp.n, "b": pb, "sweeps": st["sweeps"], "ms": st["ms"],
                 "barriers": st["barriers"], "us_per_batch": 1e3 * st["ms"] / st["barriers"], "path": st["path"]}
     TOL = 1e-4
     K = 50
