@@ -160,6 +160,39 @@ def _check(t, dtype, n, name):
         raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor with >= {n} elements")
 
 
+def _check_mdp_tensors(n, m, fmt, cost, P, row_ptr, col, prob, p_dtype, row_scale):
+    """The kernels read these arrays as flat, contiguous device memory of the types include/rmb.h
+    names; anything else (a strided view, another dtype, a host tensor) is refused here, because the
+    C ABI cannot see it.  Values are checked on the device by rmb_validate."""
+    import torch
+    if fmt not in ("dense", "csr"):
+        raise ValueError(f"format must be 'dense' or 'csr', not {fmt!r}")
+    if n < 1 or m < 1:
+        raise ValueError("need n >= 1 and m >= 1")
+    dt = {RMB_P_F32: torch.float32, RMB_P_BF16: torch.bfloat16, RMB_P_FP8E4M3: torch.uint8}.get(p_dtype)
+    if dt is None:
+        raise ValueError(f"p_dtype {p_dtype} is not one of RMB_P_F32 / RMB_P_BF16 / RMB_P_FP8E4M3")
+    _need(cost, torch.float32, n * m, "cost")
+    if fmt == "dense":
+        if p_dtype == RMB_P_FP8E4M3 and P is not None and P.dtype == getattr(torch, "float8_e4m3fn", None):
+            dt = P.dtype                     # e4m3 codes may also come as torch's own fp8 type
+        _need(P, dt, n * m * n, "P")
+        if row_scale is not None:
+            _check(row_scale, torch.float32, n * m, "row_scale")
+    else:
+        if p_dtype != RMB_P_F32:
+            raise ValueError("CSR rows are float32 (p_dtype = RMB_P_F32)")
+        _need(row_ptr, torch.int64, n * m + 1, "row_ptr")
+        _need(col, torch.int32, 0, "col")
+        _need(prob, torch.float32, col.numel(), "prob")
+
+
+def _need(t, dtype, n, name):
+    if t is None:
+        raise ValueError(f"{name} is required")
+    _check(t, dtype, n, name)
+
+
 # ----------------------------------------------------------------------------------------------
 class DeviceMDP:
     """An MDP resident in device memory (torch tensors) plus its rmb_mdp descriptor."""
@@ -168,6 +201,7 @@ class DeviceMDP:
                  k_uniform: int = 0, name: str = "", p_dtype: int = 0, row_scale=None):
         self.n, self.m, self.gamma, self.fmt, self.name = int(n), int(m), float(gamma), fmt, name
         self.cost, self.P, self.row_ptr, self.col, self.prob = cost, P, row_ptr, col, prob
+        _check_mdp_tensors(self.n, self.m, fmt, cost, P, row_ptr, col, prob, int(p_dtype), row_scale)
         self.k_uniform = int(k_uniform)
         d = rmb_mdp()
         d.n, d.m, d.gamma = self.n, self.m, self.gamma

@@ -214,3 +214,21 @@ def test_residual_kind_arguments(L):
     o.residual_kind = rmb.RMB_RESIDUAL_BELLMAN   # evaluation keeps the sweep-change test
     assert L.rmb_eval_policy(ctypes.byref(d), 4096, ctypes.byref(o), 4096, 8192, 1 << 30, None, None) == \
         rmb.RMB_ERR_UNSUPPORTED
+
+
+def test_device_mdp_refuses_unreadable_tensors():
+    """The descriptor holds raw pointers, so DeviceMDP refuses host tensors, strided views and
+    wrong element types before any of them reaches the C ABI (checked without a GPU: a host tensor
+    is refused first)."""
+    import torch
+    n, m = 4, 2
+    cost = torch.zeros(n * m)
+    P = torch.zeros(n * m * n)
+    with pytest.raises(ValueError, match="cost"):
+        rmb.DeviceMDP(n, m, 0.9, "dense", cost, P=P)
+    with pytest.raises(ValueError, match="format"):
+        rmb.DeviceMDP(n, m, 0.9, "coo", cost, P=P)
+    with pytest.raises(ValueError, match="p_dtype"):
+        rmb.DeviceMDP(n, m, 0.9, "dense", cost, P=P, p_dtype=7)
+    with pytest.raises(ValueError, match="n >= 1"):
+        rmb.DeviceMDP(0, m, 0.9, "dense", cost, P=P)
