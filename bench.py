@@ -323,12 +323,22 @@ def main():
     pe1.record(stream)
     torch.cuda.synchronize()
     ceiling = 4 * g_idx.numel() / (pe0.elapsed_time(pe1) / 1e3)
-    del g_idx, g_src
+    # the same gathers issued by the tensor-memory-access unit (tile::gather4 of 16-byte rows)
+    rmb.rmb_gather_probe_tma(g_src, g_idx, reps=1, stream=stream)
+    pe0.record(stream)
+    tma_out = rmb.rmb_gather_probe_tma(g_src, g_idx, reps=4, stream=stream)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    tma_rate = 4 * g_idx.numel() / (pe0.elapsed_time(pe1) / 1e3) if bool(torch.isfinite(tma_out).all()) else None
+    del g_idx, g_src, tma_out
     gathers = sum((st["sweeps"] + 1) * n * M_ACTIONS * K_SUCC for st in stats)
     roofline["gather_bound"] = {"rate_per_s": gathers / (kernel_ms / 1e3), "ceiling_per_s": ceiling,
                                 "frac": gathers / (kernel_ms / 1e3) / ceiling,
+                                "tma_gather4_per_s": tma_rate,
                                 "note": "random successor gathers (one 32-byte L2 sector each) vs the measured rate "
-                                        "of random 4-byte gathers from a 4 MB table (rmb_gather_probe)"}
+                                        "of random 4-byte gathers from a 4 MB table (rmb_gather_probe); "
+                                        "tma_gather4_per_s: the same gathers as tile::gather4 copies "
+                                        "(rmb_gather_probe_tma)"}
 
     # end to end through the public API: pinned host inputs copied in, V and pi copied out, every step
     e2e = None

@@ -396,6 +396,17 @@ int rmb_vi_refined(const rmb_mdp *lowp, const rmb_mdp *ref, const rmb_opts *opts
 int rmb_gather_probe(const float *src, int64_t n_src, const int32_t *idx, int64_t n_idx, int reps,
                      float *out, void *stream);
 
+/*
+ * Diagnostic (not part of the method): the same gathers issued through the tensor-memory-access unit
+ * (cp.async.bulk.tensor tile::gather4: four 16-byte rows of src, viewed as [n_src/4][4] floats, per
+ * instruction), to compare with the load path of rmb_gather_probe.  src: 16-byte aligned, n_src a
+ * multiple of 4 (< 2^32); idx: int32, 16-byte aligned, n_idx a multiple of 128; out: grid_size * 256
+ * floats (one checksum per thread, grid_size = number of SMs); a NaN checksum means a wait for a copy
+ * ran out (1 s).  Returns RMB_ERR_UNSUPPORTED when the driver has no tensor-map encoder.
+ */
+int rmb_gather_probe_tma(const float *src, int64_t n_src, const int32_t *idx, int64_t n_idx, int reps,
+                         float *out, void *stream);
+
 /* Static text for a status code. */
 const char *rmb_status_string(int status);
 

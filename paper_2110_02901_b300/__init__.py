@@ -520,6 +520,24 @@ def rmb_gather_probe(src, idx, reps: int = 1, stream=None):
     return out
 
 
+def rmb_gather_probe_tma(src, idx, reps: int = 1, stream=None):
+    """Diagnostic: the same gathers through the tensor-memory-access unit (tile::gather4 of 16-byte
+    rows); one 256-thread CTA per SM; returns the checksums (NaN where a wait ran out)."""
+    import torch
+    _check(src, torch.float32, 4, "src")
+    _check(idx, torch.int32, 128, "idx")
+    out = torch.empty(torch.cuda.get_device_properties(src.device).multi_processor_count * 256,
+                      dtype=torch.float32, device=src.device)
+    f = lib().rmb_gather_probe_tma
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    st = f(_ptr(src), src.numel(), _ptr(idx), idx.numel(), int(reps), _ptr(out), _stream_handle(stream))
+    if st != RMB_OK:
+        raise RmbError(st, "rmb_gather_probe_tma")
+    return out
+
+
 def rmb_permutation(n: int, seed: int, sweep: int, out=None, stream=None):
     """sigma_{seed,sweep}(p) for p = 0..n-1 as an int32 CUDA tensor."""
     import torch

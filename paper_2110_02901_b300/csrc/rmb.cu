@@ -4,6 +4,8 @@
 // weights, the gather-rate probe).  The persistent kernels and the device code they share live in
 // rmb_core.cuh and the per-family translation units rmb_csr.cu (CSR and batched) and rmb_dense.cu.
 
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is reached through the runtime)
+
 #include "rmb_core.cuh"
 
 namespace rmb {
@@ -260,6 +262,108 @@ __global__ void __launch_bounds__(512, 1) rmb_gather_probe_kernel(const float* _
         }
     }
     out[t] = acc;
+}
+
+// The same gathers issued by the tensor-memory-access unit instead of the load/store path:
+// cp.async.bulk.tensor tile::gather4 copies four 16-byte rows of src, viewed as [n/4][4] floats, at
+// four arbitrary row coordinates into shared memory; the lane then picks the wanted float of each
+// row.  Each warp owns a ring of kTgStages stages; a stage is one gather4 per lane (32 x 4 rows,
+// 2048 bytes of payload) completing on one mbarrier.  Every wait is bounded; a warp whose wait runs
+// out drains its copies in flight (bounded again) and writes NaN as its checksum.
+constexpr int kTgWarps = 8;
+constexpr int kTgStages = 4;
+constexpr int kTgSlot = 128;                        // bytes per gather4 destination (64 used)
+constexpr int kTgStageBytes = 32 * kTgSlot;
+constexpr int kTgSmem = kTgWarps * kTgStages * kTgStageBytes;
+
+__device__ __forceinline__ bool tg_wait(uint32_t bar, uint32_t parity, int64_t timeout_ns)
+{
+    const uint64_t t0 = globaltimer_ns();
+    uint32_t spins = 0;
+    while (!mb_try(bar, parity))
+        if ((++spins & 63u) == 0 && (int64_t)(globaltimer_ns() - t0) > timeout_ns) return false;
+    return true;
+}
+
+__global__ void __launch_bounds__(kTgWarps * 32, 1)
+rmb_gather4_probe_kernel(const __grid_constant__ CUtensorMap map, uint32_t nm1, const int4* __restrict__ idx,
+                         int64_t chunks, int reps, int64_t timeout_ns, float* __restrict__ out)
+{
+    extern __shared__ __align__(1024) unsigned char tg_ring[];
+    __shared__ __align__(8) uint64_t bars[kTgWarps][kTgStages];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * kTgWarps + w;
+    const int64_t W = (int64_t)gridDim.x * kTgWarps;
+    const uint32_t ring = (uint32_t)__cvta_generic_to_shared(tg_ring) + (uint32_t)(w * kTgStages * kTgStageBytes);
+    if (lane == 0) {
+        for (int s = 0; s < kTgStages; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bars[w][s]))
+                         : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // this warp's chunks (32 int4 of idx each): gw, gw + W, ... over reps passes of idx
+    const int64_t total = (int64_t)reps * chunks;
+    const int64_t mine = gw < total ? (total - 1 - gw) / W + 1 : 0;
+    const uint64_t map_addr = reinterpret_cast<uint64_t>(&map);
+
+    uint32_t sub[kTgStages], ph[kTgStages];
+    uint32_t inflight = 0;
+    float acc = 0.f;
+    bool ok = true;
+    auto issue = [&](int s, int64_t j) {
+        const int64_t c = (gw + j * W) % chunks;
+        const int4 v = __ldcs(idx + c * 32 + lane);
+        const uint32_t x = min((uint32_t)v.x, nm1), y = min((uint32_t)v.y, nm1);
+        const uint32_t z = min((uint32_t)v.z, nm1), q = min((uint32_t)v.w, nm1);
+        sub[s] = (x & 3u) | ((y & 3u) << 2) | ((z & 3u) << 4) | ((q & 3u) << 6);
+        const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[w][s]);
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(32 * 64) : "memory");
+        __syncwarp();
+        const uint32_t dst = ring + (uint32_t)(s * kTgStageBytes + lane * kTgSlot);
+        // this lane's earlier reads of its slot come before the copy that overwrites it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+                     " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+                     ::"r"(dst), "l"(map_addr), "r"(0), "r"((int)(x >> 2)), "r"((int)(y >> 2)), "r"((int)(z >> 2)),
+                       "r"((int)(q >> 2)), "r"(bar)
+                     : "memory");
+        inflight |= 1u << s;
+    };
+#pragma unroll
+    for (int s = 0; s < kTgStages; ++s) {
+        ph[s] = 0;
+        if (s < mine) issue(s, s);
+    }
+    for (int64_t j0 = 0; j0 < mine && ok; j0 += kTgStages) {
+#pragma unroll
+        for (int s = 0; s < kTgStages; ++s) {
+            const int64_t j = j0 + s;
+            if (j < mine && ok) {
+                const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bars[w][s]);
+                // warp-uniform outcome: issue() below holds a __syncwarp
+                if (!__all_sync(0xffffffffu, tg_wait(bar, ph[s], timeout_ns))) {
+                    ok = false;
+                } else {
+                    ph[s] ^= 1u;
+                    inflight &= ~(1u << s);
+                    const float* slot = reinterpret_cast<const float*>(tg_ring + w * kTgStages * kTgStageBytes +
+                                                                       s * kTgStageBytes + lane * kTgSlot);
+                    acc += slot[sub[s] & 3u] + slot[4 + ((sub[s] >> 2) & 3u)] + slot[8 + ((sub[s] >> 4) & 3u)] +
+                           slot[12 + ((sub[s] >> 6) & 3u)];
+                    if (j + kTgStages < mine) issue(s, j + kTgStages);
+                }
+            }
+        }
+    }
+    if (!ok) {
+        // drain the copies still in flight before the shared memory goes away
+#pragma unroll
+        for (int s = 0; s < kTgStages; ++s)
+            if (inflight & (1u << s)) tg_wait((uint32_t)__cvta_generic_to_shared(&bars[w][s]), ph[s], timeout_ns);
+    }
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = ok ? acc : __int_as_float(0x7fc00000);
 }
 
 // Row quantiser (low-precision storage of dense rows): one warp per row.
@@ -1485,6 +1589,44 @@ int rmb_gather_probe(const float* src, int64_t n_src, const int32_t* idx, int64_
     cudaFuncSetAttribute(rmb_gather_probe_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     rmb_gather_probe_kernel<<<D->sms, 512, 0, static_cast<cudaStream_t>(stream)>>>(
         src, (uint32_t)(n_src - 1), reinterpret_cast<const int4*>(idx), n_idx / 4, reps, out);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
+}
+
+int rmb_gather_probe_tma(const float* src, int64_t n_src, const int32_t* idx, int64_t n_idx, int reps, float* out,
+                         void* stream)
+{
+    if (!src || !idx || !out || n_src < 4 || (n_src & 3) || n_src >= ((int64_t)1 << 32) || n_idx < 128 ||
+        (n_idx % 128) || reps < 1)
+        return RMB_ERR_ARG;
+    if ((((uintptr_t)idx) & 15) || (((uintptr_t)src) & 15)) return RMB_ERR_ARG;
+    DevInfo* D = nullptr;
+    int st = dev_info(&D);
+    if (st) return st;
+    using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                     CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return RMB_ERR_UNSUPPORTED;
+    // src as [n/4][4] floats: 16-byte rows, a box of one row (the form gather4 takes)
+    alignas(64) CUtensorMap map;
+    const cuuint64_t dims[2] = {4, (cuuint64_t)(n_src / 4)};
+    const cuuint64_t strides[1] = {16};
+    const cuuint32_t box[2] = {4, 1};
+    const cuuint32_t estr[2] = {1, 1};
+    if (reinterpret_cast<EncodeTiled>(fn)(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(src), dims,
+                                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                          CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return RMB_ERR_ARG;
+    if (cudaFuncSetAttribute(rmb_gather4_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTgSmem) !=
+        cudaSuccess)
+        return RMB_ERR_CUDA;
+    rmb_gather4_probe_kernel<<<D->sms, kTgWarps * 32, kTgSmem, static_cast<cudaStream_t>(stream)>>>(
+        map, (uint32_t)(n_src - 1), reinterpret_cast<const int4*>(idx), n_idx / 128, reps, (int64_t)1000000000, out);
     g_launches++;
     return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
 }

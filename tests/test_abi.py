@@ -232,3 +232,17 @@ def test_device_mdp_refuses_unreadable_tensors():
         rmb.DeviceMDP(n, m, 0.9, "dense", cost, P=P, p_dtype=7)
     with pytest.raises(ValueError, match="n >= 1"):
         rmb.DeviceMDP(0, m, 0.9, "dense", cost, P=P)
+
+
+def test_gather_probe_tma_arguments(L):
+    """Argument checks of the gather4 probe, taken before any device work."""
+    f = L.rmb_gather_probe_tma
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
+                  ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(4096, 1001, 8192, 1024, 1, 4096, None) == rmb.RMB_ERR_ARG      # n_src not a multiple of 4
+    assert f(4096, 1000, 8192, 1000, 1, 4096, None) == rmb.RMB_ERR_ARG      # n_idx not a multiple of 128
+    assert f(4096, 1000, 8200, 1024, 1, 4096, None) == rmb.RMB_ERR_ARG      # idx not 16-byte aligned
+    assert f(4100, 1000, 8192, 1024, 1, 4096, None) == rmb.RMB_ERR_ARG      # src not 16-byte aligned
+    assert f(4096, 1000, 8192, 1024, 0, 4096, None) == rmb.RMB_ERR_ARG      # reps < 1
+    assert f(None, 1000, 8192, 1024, 1, 4096, None) == rmb.RMB_ERR_ARG
