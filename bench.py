@@ -36,6 +36,9 @@ METRIC = "time-to-1e-6 residual and Bellman backups/s vs batch b; P-stream HBM G
 N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
 CSR_DRAM_BYTES_PER_STATE_PASS = (11168375296 + 11002624) / (21 * 262144)
+# batched launch: DRAM bytes (read + write) over the algorithmic row bytes, from one ncu capture of the
+# 256-MDP launch with every MDP capped at 20 sweeps (74.0996 GB + 0.3744 GB over 72.0046 GB)
+BATCHED_DRAM_PER_ALGO_BYTE = (74.099613e9 + 374434304) / 72004641408
 DENSE_DRAM_BYTES_PER_P_BYTE = (4285128192 + 3765760) / (4 * 4096 * 16 * 4096 * 4)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]
 HEADLINE_B = 262144
@@ -620,6 +623,20 @@ def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
     for x in mdps:
         Vs.append(Vall[off:off + x.n])
         off += x.n
+    if args.profile_case:
+        # profiling mode: the same launch (same plan), every MDP capped at profile_case sweeps
+        o = rmb.Opts(batch=1, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=args.profile_case, validate=False)
+        s = torch.cuda.Stream()
+        B = rmb.Batch(dms, Vs, o, stream=s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        B.run(s)
+        e1.record(s)
+        torch.cuda.synchronize()
+        res = B.results(stream=s, check=False)
+        return {"profile_case": True, "mdps": len(mdps), "ms": e0.elapsed_time(e1),
+                "sweeps_total": sum(r["sweeps"] for r in res),
+                "nnz_pass_bytes": sum((r["sweeps"] + 1) * x.nnz * 8 for x, r in zip(mdps, res))}
     o = rmb.Opts(batch=1, seed=mdpgen.PERM_SEED, eps=EPS, max_sweeps=200000, validate=False)
     s = torch.cuda.Stream()
     B = rmb.Batch(dms, Vs, o, stream=s)
@@ -681,7 +698,10 @@ def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
                   "groups": sorted({p["group_ctas"] for p in plan}),
                   "max_sweeps": max(r["sweeps"] for r in res)},
                  roofline={"bound": "hbm", "achieved": nnz_passes / (ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                           "frac": nnz_passes / (ms / 1e3) / 1e9 / hbm, "traffic": None,
+                           "frac": nnz_passes / (ms / 1e3) / 1e9 / hbm,
+                           "traffic": BATCHED_DRAM_PER_ALGO_BYTE * nnz_passes,
+                           "traffic_note": "ncu DRAM bytes / algorithmic bytes of the same launch capped at 20 "
+                                           "sweeps per MDP (1.034), times this run's algorithmic bytes",
                            "kernel": "rmb_batched_kernel", "peak_kind": peak_kind},
                  cpu_baseline=cpu)
 
