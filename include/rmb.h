@@ -342,14 +342,15 @@ typedef struct {
 
 typedef struct {
     int64_t batch;         /* chosen b */
-    int32_t group_ctas;    /* CTAs solving this MDP together (1 = alone, packed with others) */
-    int32_t first_cta;
+    int32_t group_ctas;    /* CTAs solving this MDP together (1 = alone: taken from a shared queue,
+                              longest estimate first, by whichever CTA is free) */
+    int32_t first_cta;     /* first CTA of the group; -1 for an MDP solved alone (queue) */
     double est_ms;         /* cost-model estimate of this MDP's solve time */
 } rmb_batch_plan_item;
 
 typedef struct {
     void *workspace;
-    int32_t count, grid_ctas, ntasks, reserved;
+    int32_t count, grid_ctas, ntasks, nqueue;   /* nqueue: single-CTA MDPs in the shared queue */
     int64_t ctrl_offset, kp_offset, toff_offset, tasks_offset;
     double est_ms;         /* cost-model makespan */
 } rmb_batch_handle;

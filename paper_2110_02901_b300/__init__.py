@@ -91,7 +91,7 @@ class rmb_batch_plan_item(ctypes.Structure):
 
 class rmb_batch_handle(ctypes.Structure):
     _fields_ = [("workspace", ctypes.c_void_p), ("count", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
-                ("ntasks", ctypes.c_int32), ("reserved", ctypes.c_int32), ("ctrl_offset", ctypes.c_int64),
+                ("ntasks", ctypes.c_int32), ("nqueue", ctypes.c_int32), ("ctrl_offset", ctypes.c_int64),
                 ("kp_offset", ctypes.c_int64), ("toff_offset", ctypes.c_int64), ("tasks_offset", ctypes.c_int64),
                 ("est_ms", ctypes.c_double)]
 

@@ -921,6 +921,7 @@ int noalloc_scratch(void** out)
 // Each MDP gets the b minimising its time (unless the caller fixed b).  The makespan target M is
 // found by bisection: MDPs whose single-CTA time exceeds M get the smallest group that meets M, the
 // others are packed onto the remaining CTAs longest-first (LPT); M is feasible if every CTA meets it.
+// The packing only decides feasibility: at run time the single-CTA MDPs come from one shared queue.
 // ------------------------------------------------------------------------------------------------
 struct ItemCost {
     int64_t n;
@@ -1009,7 +1010,8 @@ struct BatchPlan {
     std::vector<ItemPlan> items;
     std::vector<int> first_cta;
     std::vector<int> task_off;
-    std::vector<BatchTask> tasks;
+    std::vector<BatchTask> tasks;   // per-CTA static tasks (task_off), then the queue of single-CTA MDPs
+    int nqueue = 0;
     double makespan;
 };
 
@@ -1067,17 +1069,16 @@ bool try_makespan(const std::vector<ItemCost>& cs, const std::vector<int64_t>& f
         cta += ip[i].G;
         mk = ip[i].t > mk ? ip[i].t : mk;
     }
-    for (size_t bI = 0; bI < bins.size(); ++bI) {
-        for (int i : bins[bI]) {
-            out->first_cta[i] = cta + (int)bI;
-            per[cta + bI].push_back(BatchTask{i, 0, 1, 0});
-        }
-        mk = load[bI] > mk ? load[bI] : mk;
-    }
+    // the bins only prove M feasible: single-CTA MDPs are dispatched at run time from one queue,
+    // longest first, to whichever CTA is free (the groups' CTAs too, once their MDP is solved), so
+    // errors of the cost model do not leave CTAs idle
+    for (size_t bI = 0; bI < bins.size(); ++bI) mk = load[bI] > mk ? load[bI] : mk;
     for (int c = 0; c < ctas; ++c) {
         out->task_off[c + 1] = out->task_off[c] + (int)per[c].size();
         for (const BatchTask& t : per[c]) out->tasks.push_back(t);
     }
+    for (int i : small) out->tasks.push_back(BatchTask{i, 0, 1, 0});   // sorted longest first above
+    out->nqueue = (int)small.size();
     out->makespan = mk;
     return true;
 }
@@ -1241,6 +1242,7 @@ int rmb_batched_plan(const rmb_batch_item* items, int count, const rmb_opts* opt
     handle->count = count;
     handle->grid_ctas = ctas;
     handle->ntasks = (int32_t)plan.tasks.size();
+    handle->nqueue = plan.nqueue;
     handle->ctrl_offset = (int64_t)B.ctrl;
     handle->kp_offset = (int64_t)B.kps;
     handle->toff_offset = (int64_t)B.toff;
@@ -1254,11 +1256,17 @@ int rmb_batched_run(const rmb_batch_handle* h, void* stream)
     if (!h || !h->workspace || h->count < 1 || h->grid_ctas < 1) return RMB_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     char* ws = static_cast<char*>(h->workspace);
-    if (cudaMemsetAsync(ws + h->ctrl_offset, 0, (size_t)h->count * sizeof(Ctrl), s) != cudaSuccess) return RMB_ERR_CUDA;
+    if (h->nqueue < 0 || h->nqueue > h->count) return RMB_ERR_ARG;
+    // control blocks and the queue cursor (the first 4 bytes of the workspace)
+    if (cudaMemsetAsync(ws + h->ctrl_offset, 0, (size_t)h->count * sizeof(Ctrl), s) != cudaSuccess ||
+        cudaMemsetAsync(ws, 0, sizeof(int), s) != cudaSuccess)
+        return RMB_ERR_CUDA;
     const KP* kps = reinterpret_cast<const KP*>(ws + h->kp_offset);
     const int* toff = reinterpret_cast<const int*>(ws + h->toff_offset);
     const BatchTask* tasks = reinterpret_cast<const BatchTask*>(ws + h->tasks_offset);
-    void* args[] = {(void*)&kps, (void*)&toff, (void*)&tasks};
+    int nqueue = h->nqueue;
+    int* qnext = reinterpret_cast<int*>(ws);
+    void* args[] = {(void*)&kps, (void*)&toff, (void*)&tasks, (void*)&nqueue, (void*)&qnext};
     const cudaError_t ce = cudaLaunchCooperativeKernel(batched_kernel_ptr(),
                                                        dim3(h->grid_ctas), dim3(kCsrThreads), args, 0, s);
     g_launches++;

@@ -36,13 +36,27 @@ const void* csr_vec_kernel_for(int nca, int nco)
 const void* csr_gen_kernel_ptr() { return reinterpret_cast<const void*>(rmb_csr_gen_kernel); }
 
 __global__ void __launch_bounds__(kCsrThreads, 1)
-rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off, const BatchTask* __restrict__ tasks)
+rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off, const BatchTask* __restrict__ tasks,
+                   int nqueue, int* __restrict__ qnext)
 {
     __shared__ RedSmem rs;
     __shared__ KP s_kp;
+    __shared__ int s_next;
+    // this CTA's own tasks (its share of the multi-CTA groups) first, then single-CTA MDPs from the
+    // shared queue (longest first, after the last static task) until it is empty
     const int t0 = task_off[blockIdx.x], t1 = task_off[blockIdx.x + 1];
-    for (int t = t0; t < t1; ++t) {
-        const BatchTask bt = tasks[t];
+    const int nstatic = task_off[gridDim.x];
+    for (int t = t0;; ++t) {
+        BatchTask bt;
+        if (t < t1) {
+            bt = tasks[t];
+        } else {
+            __syncthreads();   // every thread has read the previous s_next
+            if (threadIdx.x == 0) s_next = atomicAdd(qnext, 1);
+            __syncthreads();
+            if (s_next >= nqueue) break;
+            bt = tasks[nstatic + s_next];
+        }
         __syncthreads();
         if (threadIdx.x == 0) s_kp = kps[bt.item];
         __syncthreads();
