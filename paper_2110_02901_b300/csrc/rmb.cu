@@ -920,8 +920,8 @@ int noalloc_scratch(void** out)
 //   time       = sweeps(b) * ceil(n/b) * batch time
 // Each MDP gets the b minimising its time (unless the caller fixed b).  The makespan target M is
 // found by bisection: MDPs whose single-CTA time exceeds M get the smallest group that meets M, the
-// others are packed onto the remaining CTAs longest-first (LPT); M is feasible if every CTA meets it.
-// The packing only decides feasibility: at run time the single-CTA MDPs come from one shared queue.
+// others are packed longest-first (LPT) onto the CTA that frees first, as the run-time queue does:
+// free CTAs from time 0, a group's CTAs from the end of its MDP; M is feasible if every CTA meets it.
 // ------------------------------------------------------------------------------------------------
 struct ItemCost {
     int64_t n;
@@ -1043,16 +1043,19 @@ bool try_makespan(const std::vector<ItemCost>& cs, const std::vector<int64_t>& f
         big.push_back(i);
     }
     const int free_ctas = ctas - used;
-    if (free_ctas < 0 || (free_ctas == 0 && !small.empty())) return false;
+    if (free_ctas < 0) return false;
     std::sort(small.begin(), small.end(), [&](int a, int b) { return ip[a].t > ip[b].t; });
-    std::vector<double> load(free_ctas > 0 ? free_ctas : 0, 0.0);
-    std::vector<std::vector<int>> bins(load.size());
+    // the run-time queue is list scheduling: the CTA that frees first takes the next MDP, longest
+    // first.  Free CTAs start at 0; a group's CTAs join once their MDP is solved.
+    std::vector<double> load(free_ctas, 0.0);
+    for (int i : big)
+        for (int r = 0; r < ip[i].G; ++r) load.push_back(ip[i].t);
+    if (load.empty() && !small.empty()) return false;
     for (int i : small) {
         int best = 0;
         for (int c = 1; c < (int)load.size(); ++c)
             if (load[c] < load[best]) best = c;
         load[best] += ip[i].t;
-        bins[best].push_back(i);
         if (load[best] > M) return false;
     }
     if (!out) return true;
@@ -1072,7 +1075,7 @@ bool try_makespan(const std::vector<ItemCost>& cs, const std::vector<int64_t>& f
     // the bins only prove M feasible: single-CTA MDPs are dispatched at run time from one queue,
     // longest first, to whichever CTA is free (the groups' CTAs too, once their MDP is solved), so
     // errors of the cost model do not leave CTAs idle
-    for (size_t bI = 0; bI < bins.size(); ++bI) mk = load[bI] > mk ? load[bI] : mk;
+    for (double l : load) mk = l > mk ? l : mk;
     for (int c = 0; c < ctas; ++c) {
         out->task_off[c + 1] = out->task_off[c] + (int)per[c].size();
         for (const BatchTask& t : per[c]) out->tasks.push_back(t);
