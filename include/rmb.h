@@ -319,9 +319,11 @@ int rmb_fixed_point_grad(const rmb_mdp *mdp, const int32_t *pi, const float *V, 
 /*
  * Batched MB-VI: many independent MDPs (RMB_CSR) solved in one persistent launch (the paper has one
  * MDP per solve; this runs its MB-VI, eq. (11), on each).  A host-side autotuner picks every MDP's
- * batch size b (unless fixed) and the number of CTAs that solve it from a cost model, and packs small
- * MDPs onto single CTAs longest-first.  Results per MDP are identical to rmb_vi with the same b, seed
- * and options.
+ * batch size b (unless fixed) and the number of CTAs that solve it from a cost model.  MDPs solved by
+ * a single CTA are taken at run time from one shared queue, longest estimate first, by whichever CTA
+ * is free (a group's CTAs join once their MDP is solved); the workspace's first 4 bytes hold the
+ * queue cursor, which rmb_batched_run resets.  Results per MDP are identical to rmb_vi with the same
+ * b, seed and options.
  *
  * 1. rmb_batched_workspace_bytes(items, count, opts): workspace size for this plan.
  * 2. rmb_batched_plan(...): plans, writes the kernel parameters into the workspace (synchronous) and
