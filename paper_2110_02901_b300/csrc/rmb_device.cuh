@@ -199,7 +199,8 @@ __device__ __forceinline__ void grid_arrive(Ctrl* c, unsigned long long& target,
     if (gsize == 1) return;   // a one-CTA group synchronises with the CTA barrier alone
     if (threadIdx.x == 0) {
         target += gsize;
-        __threadfence();
+        // the release add publishes the CTA's writes: they are ordered before it by the CTA barrier
+        // above, and release is cumulative, so no separate fence is needed
         if (!skip_arrive) red_release_add_u64(&c->bar, 1ull);
     }
 }
