@@ -35,11 +35,11 @@ import mdpgen  # noqa: E402
 METRIC = "time-to-1e-6 residual and Bellman backups/s vs batch b; P-stream HBM GB/s"
 N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
-CSR_DRAM_BYTES_PER_STATE_PASS = (11168375296 + 11002624) / (21 * 262144)
+CSR_DRAM_BYTES_PER_STATE_PASS = (11167924480 + 10862336) / (21 * 262144)
 # batched launch: DRAM bytes (read + write) over the algorithmic row bytes, from one ncu capture of the
-# 256-MDP launch with every MDP capped at 20 sweeps (75.1119 GB + 0.4646 GB over 72.0046 GB)
-BATCHED_DRAM_PER_ALGO_BYTE = (75.111940e9 + 464600064) / 72004641408
-DENSE_DRAM_BYTES_PER_P_BYTE = (4285128192 + 3765760) / (4 * 4096 * 16 * 4096 * 4)
+# 256-MDP launch with every MDP capped at 20 sweeps (74.8343 GB + 0.4083 GB over 72.0046 GB)
+BATCHED_DRAM_PER_ALGO_BYTE = (74834331392 + 408346112) / 72004641408
+DENSE_DRAM_BYTES_PER_P_BYTE = (4285011968 + 3790336) / (4 * 4096 * 16 * 4096 * 4)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]
 HEADLINE_B = 262144
 MPI_K = 10
@@ -701,7 +701,7 @@ def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
                            "frac": nnz_passes / (ms / 1e3) / 1e9 / hbm,
                            "traffic": BATCHED_DRAM_PER_ALGO_BYTE * nnz_passes,
                            "traffic_note": "ncu DRAM bytes / algorithmic bytes of the same launch capped at 20 "
-                                           "sweeps per MDP (1.050), times this run's algorithmic bytes",
+                                           "sweeps per MDP (1.045), times this run's algorithmic bytes",
                            "kernel": "rmb_batched_kernel", "peak_kind": peak_kind},
                  cpu_baseline=cpu)
 
