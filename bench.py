@@ -319,17 +319,17 @@ def main():
     g_idx = torch.randint(0, n, (1 << 27,), dtype=torch.int32, device=dev,
                           generator=torch.Generator(device=dev).manual_seed(7))
     g_src = torch.rand(n, dtype=torch.float32, device=dev)
-    rmb.rmb_gather_probe(g_src, g_idx, reps=1, stream=stream)
+    rmb.rmb_diag_gather_probe(g_src, g_idx, reps=1, stream=stream)
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pe0.record(stream)
-    rmb.rmb_gather_probe(g_src, g_idx, reps=4, stream=stream)
+    rmb.rmb_diag_gather_probe(g_src, g_idx, reps=4, stream=stream)
     pe1.record(stream)
     torch.cuda.synchronize()
     ceiling = 4 * g_idx.numel() / (pe0.elapsed_time(pe1) / 1e3)
     # the same gathers issued by the tensor-memory-access unit (tile::gather4 of 16-byte rows)
-    rmb.rmb_gather_probe_tma(g_src, g_idx, reps=1, stream=stream)
+    rmb.rmb_diag_gather_probe_tma(g_src, g_idx, reps=1, stream=stream)
     pe0.record(stream)
-    tma_out = rmb.rmb_gather_probe_tma(g_src, g_idx, reps=4, stream=stream)
+    tma_out = rmb.rmb_diag_gather_probe_tma(g_src, g_idx, reps=4, stream=stream)
     pe1.record(stream)
     torch.cuda.synchronize()
     tma_rate = 4 * g_idx.numel() / (pe0.elapsed_time(pe1) / 1e3) if bool(torch.isfinite(tma_out).all()) else None
@@ -339,9 +339,9 @@ def main():
                                 "frac": gathers / (kernel_ms / 1e3) / ceiling,
                                 "tma_gather4_per_s": tma_rate,
                                 "note": "random successor gathers (one 32-byte L2 sector each) vs the measured rate "
-                                        "of random 4-byte gathers from a 4 MB table (rmb_gather_probe); "
+                                        "of random 4-byte gathers from a 4 MB table (rmb_diag_gather_probe); "
                                         "tma_gather4_per_s: the same gathers as tile::gather4 copies "
-                                        "(rmb_gather_probe_tma)"}
+                                        "(rmb_diag_gather_probe_tma)"}
 
     # end to end through the public API: pinned host inputs copied in, V and pi copied out, every step
     e2e = None

@@ -268,7 +268,8 @@ int rmb_validate(const rmb_mdp *mdp, void *workspace, size_t workspace_bytes, vo
  * (each call clears the parts that must start at zero).  Calls that overlap on the GPU -- on
  * different streams or from different host threads -- race on the array and give wrong results;
  * serialise them.
- * stats (optional): as for rmb_vi except ms = 0, grid_ctas = 0, path = -1, lanes_per_state = 0.
+ * stats (optional): as for rmb_vi (batch included) except ms = 0, grid_ctas = 0, path = -1,
+ * lanes_per_state = 0.
  */
 #define RMB_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 int rmb_vi_noalloc(const rmb_mdp *mdp, const rmb_opts *opts, float *V_inout, int32_t *pi_out,
@@ -288,6 +289,25 @@ int rmb_vi_noalloc(const rmb_mdp *mdp, const rmb_opts *opts, float *V_inout, int
 size_t rmb_residual_weights_workspace_bytes(const rmb_mdp *mdp);
 int rmb_residual_weights(const rmb_mdp *mdp, const float *V, float floor_frac, uint32_t *weights_out,
                          void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * MB-VI with importance-sampled batches (Sec. V suggests importance sampling and epsilon-greedy
+ * selection of the batch states; the refresh rule is the library's): in rounds,
+ *   weights = rmb_residual_weights(V, floor_frac);
+ *   up to `refresh` sweeps of MB-VI whose batches are drawn with RMB_SELECT_WEIGHTED by those weights
+ *   (the sweep counter of the draws runs on across rounds);
+ * until a sweep's change <= opts->eps is confirmed by ||TV - V||_inf <= opts->eps (the stop rule of
+ * draws), or opts->max_sweeps sweeps in all (then RMB_ERR_NOT_CONVERGED).  opts->select, weights,
+ * residual_kind and trace are ignored; RMB_FLAG_ASYNC is unsupported.  refresh >= 1, floor_frac in
+ * [0, 1].  V_inout, pi_out, qgap_out as for rmb_vi.
+ *   workspace: rmb_vi_prioritized_workspace_bytes(mdp, opts) bytes, 256-byte aligned.
+ * Synchronous: each round's status is read on the host.  stats (optional): sweeps in all,
+ * iters = rounds, barriers in all, ms = device time of the whole call, the rest from the last round.
+ */
+size_t rmb_vi_prioritized_workspace_bytes(const rmb_mdp *mdp, const rmb_opts *opts);
+int rmb_vi_prioritized(const rmb_mdp *mdp, const rmb_opts *opts, int32_t refresh, float floor_frac,
+                       float *V_inout, int32_t *pi_out, float *qgap_out, void *workspace,
+                       size_t workspace_bytes, rmb_stats *stats, void *stream);
 
 /*
  * P(.|s,a) = softmax of the row's logits over its k successors (RMB_CSR with k_uniform = k > 0):
@@ -388,27 +408,6 @@ int rmb_quantize_rows(const float *P, int64_t rows, int64_t cols, int32_t p_dtyp
 int rmb_vi_refined(const rmb_mdp *lowp, const rmb_mdp *ref, const rmb_opts *opts, double eps_low,
                    float *V_inout, int32_t *pi_out, float *qgap_out, void *workspace,
                    size_t workspace_bytes, rmb_stats *stats_low, rmb_stats *stats_ref, void *stream);
-
-/*
- * Diagnostic (not part of the method): the attainable rate of random 4-byte gathers.  One CTA of 512
- * threads per SM streams idx (int32, 16-byte aligned, n_idx a multiple of 4) and gathers src[idx]
- * through L1, reps times; out receives one checksum per thread (grid_size * 512 floats, grid_size =
- * number of SMs).  With src sized like the value vector and uniformly random idx this measures the
- * L1->L2 request ceiling that bounds the CSR sweeps.
- */
-int rmb_gather_probe(const float *src, int64_t n_src, const int32_t *idx, int64_t n_idx, int reps,
-                     float *out, void *stream);
-
-/*
- * Diagnostic (not part of the method): the same gathers issued through the tensor-memory-access unit
- * (cp.async.bulk.tensor tile::gather4: four 16-byte rows of src, viewed as [n_src/4][4] floats, per
- * instruction), to compare with the load path of rmb_gather_probe.  src: 16-byte aligned, n_src a
- * multiple of 4 (< 2^32); idx: int32, 16-byte aligned, n_idx a multiple of 128; out: grid_size * 256
- * floats (one checksum per thread, grid_size = number of SMs); a NaN checksum means a wait for a copy
- * ran out (1 s).  Returns RMB_ERR_UNSUPPORTED when the driver has no tensor-map encoder.
- */
-int rmb_gather_probe_tma(const float *src, int64_t n_src, const int32_t *idx, int64_t n_idx, int reps,
-                         float *out, void *stream);
 
 /* Static text for a status code. */
 const char *rmb_status_string(int status);

@@ -350,20 +350,42 @@ def rmb_residual_weights(mdp: DeviceMDP, V, floor_frac: float = 0.05, out=None, 
     return out
 
 
-def prioritized_vi(mdp: DeviceMDP, V, batch: int, eps: float, refresh: int = 4, floor_frac: float = 0.05,
-                   seed: int = 12345, max_rounds: int = 100000, pi=None, stream=None):
+def rmb_vi_prioritized(mdp: DeviceMDP, opts: Opts, V, refresh: int = 4, floor_frac: float = 0.05, pi=None, qgap=None,
+                       ws=None, stats: bool = True, stream=None, check: bool = True):
     """MB-VI whose batches are drawn by residual weights, refreshed every `refresh` sweeps (the
-    importance-sampled selection suggested in Sec. V); stops when ||TV - V||_inf <= eps.
-    Returns dict(sweeps, rounds, residual, status)."""
-    sweeps = 0
-    for r in range(max_rounds):
-        w = rmb_residual_weights(mdp, V, floor_frac, stream=stream)
-        st = rmb_vi(mdp, Opts(batch=batch, seed=seed, eps=eps, max_sweeps=refresh, start_sweep=sweeps,
-                              validate=False, select=RMB_SELECT_WEIGHTED, weights=w), V, pi, stream=stream)
-        sweeps += st["sweeps"]
-        if st["status"] == RMB_OK:
-            return {"sweeps": sweeps, "rounds": r + 1, "residual": st["residual"], "status": RMB_OK}
-    return {"sweeps": sweeps, "rounds": max_rounds, "residual": st["residual"], "status": RMB_ERR_NOT_CONVERGED}
+    importance-sampled selection suggested in Sec. V); stops when a sweep's change and
+    ||TV - V||_inf are <= opts.eps.  Returns the stats dict (iters = rounds)."""
+    import torch
+    _check(V, torch.float32, mdp.n, "V")
+    _check(pi, torch.int32, mdp.n, "pi")
+    _check(qgap, torch.float32, mdp.n, "qgap")
+    L = lib()
+    L.rmb_vi_prioritized_workspace_bytes.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.POINTER(rmb_opts)]
+    L.rmb_vi_prioritized_workspace_bytes.restype = ctypes.c_size_t
+    L.rmb_vi_prioritized.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.POINTER(rmb_opts), ctypes.c_int32, ctypes.c_float,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_size_t, ctypes.POINTER(rmb_stats), ctypes.c_void_p]
+    L.rmb_vi_prioritized.restype = ctypes.c_int
+    o = opts.desc()
+    if ws is None:
+        nb = int(L.rmb_vi_prioritized_workspace_bytes(ctypes.byref(mdp.desc), ctypes.byref(o)))
+        if nb == 0:
+            raise RmbError(RMB_ERR_ARG, "rmb_vi_prioritized_workspace_bytes")
+        ws = torch.empty(nb, dtype=torch.uint8, device=V.device)
+    s = rmb_stats() if stats else None
+    st = L.rmb_vi_prioritized(ctypes.byref(mdp.desc), ctypes.byref(o), int(refresh), float(floor_frac), _ptr(V),
+                              _ptr(pi), _ptr(qgap), _ptr(ws), ws.numel(), ctypes.byref(s) if s is not None else None,
+                              _stream_handle(stream))
+    return _finish(st, s, "rmb_vi_prioritized") if check else (st, s.as_dict() if s is not None else None)
+
+
+def prioritized_vi(mdp: DeviceMDP, V, batch: int, eps: float, refresh: int = 4, floor_frac: float = 0.05,
+                   seed: int = 12345, max_sweeps: int = 1000000, pi=None, stream=None):
+    """rmb_vi_prioritized with the options spelled out; returns dict(sweeps, rounds, residual, status)."""
+    st = rmb_vi_prioritized(mdp, Opts(batch=batch, seed=seed, eps=eps, max_sweeps=max_sweeps, validate=False), V,
+                            refresh=refresh, floor_frac=floor_frac, pi=pi, stream=stream)
+    return {"sweeps": st["sweeps"], "rounds": st["iters"], "residual": st["residual"], "status": st["status"],
+            "ms": st["ms"]}
 
 
 def rmb_greedy(mdp: DeviceMDP, V, TV=None, pi=None, qgap=None, opts: Optional[Opts] = None, ws=None,
@@ -503,24 +525,24 @@ def rmb_vi_refined(lowp: DeviceMDP, ref: DeviceMDP, opts: Opts, eps_low: float, 
     return s1.as_dict(), s2.as_dict()
 
 
-def rmb_gather_probe(src, idx, reps: int = 1, stream=None):
+def rmb_diag_gather_probe(src, idx, reps: int = 1, stream=None):
     """Diagnostic: gather src[idx] (reps times) with one 512-thread CTA per SM; returns the checksums."""
     import torch
     _check(src, torch.float32, 1, "src")
     _check(idx, torch.int32, 4, "idx")
     out = torch.empty(torch.cuda.get_device_properties(src.device).multi_processor_count * 512,
                       dtype=torch.float32, device=src.device)
-    f = lib().rmb_gather_probe
+    f = lib().rmb_diag_gather_probe
     f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                   ctypes.c_void_p]
     f.restype = ctypes.c_int
     st = f(_ptr(src), src.numel(), _ptr(idx), idx.numel(), int(reps), _ptr(out), _stream_handle(stream))
     if st != RMB_OK:
-        raise RmbError(st, "rmb_gather_probe")
+        raise RmbError(st, "rmb_diag_gather_probe")
     return out
 
 
-def rmb_gather_probe_tma(src, idx, reps: int = 1, stream=None):
+def rmb_diag_gather_probe_tma(src, idx, reps: int = 1, stream=None):
     """Diagnostic: the same gathers through the tensor-memory-access unit (tile::gather4 of 16-byte
     rows); one 256-thread CTA per SM; returns the checksums (NaN where a wait ran out)."""
     import torch
@@ -528,13 +550,13 @@ def rmb_gather_probe_tma(src, idx, reps: int = 1, stream=None):
     _check(idx, torch.int32, 128, "idx")
     out = torch.empty(torch.cuda.get_device_properties(src.device).multi_processor_count * 256,
                       dtype=torch.float32, device=src.device)
-    f = lib().rmb_gather_probe_tma
+    f = lib().rmb_diag_gather_probe_tma
     f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                   ctypes.c_void_p]
     f.restype = ctypes.c_int
     st = f(_ptr(src), src.numel(), _ptr(idx), idx.numel(), int(reps), _ptr(out), _stream_handle(stream))
     if st != RMB_OK:
-        raise RmbError(st, "rmb_gather_probe_tma")
+        raise RmbError(st, "rmb_diag_gather_probe_tma")
     return out
 
 

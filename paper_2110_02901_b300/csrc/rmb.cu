@@ -7,6 +7,7 @@
 #include <cuda.h>   // CUtensorMap and its enums (the encoder is reached through the runtime)
 
 #include "rmb_core.cuh"
+#include "rmb_diag.h"
 
 namespace rmb {
 
@@ -1468,6 +1469,89 @@ int rmb_residual_weights(const rmb_mdp* mdp, const float* V, float floor_frac, u
     return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
 }
 
+// workspace of rmb_vi_prioritized: weights [n] | the residual-weights pass | the weighted MB-VI solve
+static size_t prioritized_parts(const rmb_mdp* mdp, const rmb_opts* opts, size_t* off_rw, size_t* off_vi)
+{
+    if (check_mdp(mdp) || !opts) return 0;
+    rmb_opts o = *opts;
+    o.select = RMB_SELECT_WEIGHTED;
+    const size_t vi = rmb_workspace_bytes(mdp, &o);
+    const size_t rw = rmb_residual_weights_workspace_bytes(mdp);
+    if (vi == 0 || rw == 0) return 0;
+    *off_rw = align_up((size_t)mdp->n * 4, 256);
+    *off_vi = *off_rw + align_up(rw, 256);
+    return *off_vi + vi;
+}
+
+size_t rmb_vi_prioritized_workspace_bytes(const rmb_mdp* mdp, const rmb_opts* opts)
+{
+    size_t a, b;
+    return prioritized_parts(mdp, opts, &a, &b);
+}
+
+int rmb_vi_prioritized(const rmb_mdp* mdp, const rmb_opts* opts, int32_t refresh, float floor_frac, float* V_inout,
+                       int32_t* pi_out, float* qgap_out, void* workspace, size_t workspace_bytes, rmb_stats* stats,
+                       void* stream)
+{
+    int st = check_mdp(mdp);
+    if (st) return st;
+    if (!opts || !V_inout || refresh < 1 || !(floor_frac >= 0.f && floor_frac <= 1.f)) return RMB_ERR_ARG;
+    if (opts->max_sweeps < 1 || !(opts->eps >= 0.0) || std::isinf(opts->eps) || opts->start_sweep < 0)
+        return RMB_ERR_ARG;
+    if (opts->flags & RMB_FLAG_ASYNC) return RMB_ERR_UNSUPPORTED;
+    size_t off_rw = 0, off_vi = 0;
+    const size_t need = prioritized_parts(mdp, opts, &off_rw, &off_vi);
+    if (need == 0) return RMB_ERR_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255)) return RMB_ERR_WORKSPACE;
+    if (workspace_bytes < need) return RMB_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    uint32_t* w = reinterpret_cast<uint32_t*>(ws);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (stats) {
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return RMB_ERR_CUDA;
+        cudaEventRecord(e0, s);
+    }
+    rmb_opts o = *opts;
+    o.select = RMB_SELECT_WEIGHTED;
+    o.weights = w;
+    o.residual_kind = RMB_RESIDUAL_SWEEP;   // draws always confirm with the full residual
+    o.trace = nullptr;
+    int64_t sweeps = 0, rounds = 0, barriers = 0;
+    rmb_stats r;
+    std::memset(&r, 0, sizeof(r));
+    int status = RMB_ERR_NOT_CONVERGED;
+    while (sweeps < opts->max_sweeps) {
+        // one round: weights from the residual at the current values, then up to `refresh` sweeps of
+        // weighted draws (the solve stops early once its change and ||TV - V||_inf are <= eps)
+        if ((st = rmb_residual_weights(mdp, V_inout, floor_frac, w, ws + off_rw, off_vi - off_rw, stream))) return st;
+        o.start_sweep = opts->start_sweep + sweeps;
+        o.max_sweeps = std::min<int64_t>(refresh, opts->max_sweeps - sweeps);
+        o.validate = rounds == 0 ? opts->validate : 0;
+        st = rmb_vi(mdp, &o, V_inout, pi_out, qgap_out, ws + off_vi, workspace_bytes - off_vi, &r, stream);
+        ++rounds;
+        sweeps += r.sweeps;
+        barriers += r.barriers;
+        if (st == RMB_OK) { status = RMB_OK; break; }
+        if (st != RMB_ERR_NOT_CONVERGED) { status = st; break; }
+        if (r.sweeps == 0) break;
+    }
+    if (!stats) return status;
+    cudaEventRecord(e1, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *stats = r;
+    stats->sweeps = sweeps;
+    stats->iters = rounds;
+    stats->barriers = barriers;
+    stats->status = status;
+    stats->ms = ms;
+    return status;
+}
+
 size_t rmb_fixed_point_grad_workspace_bytes(const rmb_mdp* mdp, const rmb_opts* opts)
 {
     if (check_mdp(mdp) || mdp->format != RMB_CSR || mdp->k_uniform <= 0) return 0;
@@ -1588,7 +1672,7 @@ int rmb_vi_refined(const rmb_mdp* lowp, const rmb_mdp* ref, const rmb_opts* opts
     return solve(q2);
 }
 
-int rmb_gather_probe(const float* src, int64_t n_src, const int32_t* idx, int64_t n_idx, int reps, float* out,
+int rmb_diag_gather_probe(const float* src, int64_t n_src, const int32_t* idx, int64_t n_idx, int reps, float* out,
                      void* stream)
 {
     if (!src || !idx || !out || n_src < 1 || n_src >= ((int64_t)1 << 32) || n_idx < 4 || (n_idx & 3) || reps < 1)
@@ -1604,7 +1688,7 @@ int rmb_gather_probe(const float* src, int64_t n_src, const int32_t* idx, int64_
     return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
 }
 
-int rmb_gather_probe_tma(const float* src, int64_t n_src, const int32_t* idx, int64_t n_idx, int reps, float* out,
+int rmb_diag_gather_probe_tma(const float* src, int64_t n_src, const int32_t* idx, int64_t n_idx, int reps, float* out,
                          void* stream)
 {
     if (!src || !idx || !out || n_src < 4 || (n_src & 3) || n_src >= ((int64_t)1 << 32) || n_idx < 128 ||
@@ -1683,6 +1767,8 @@ int rmb_vi_noalloc(const rmb_mdp* mdp, const rmb_opts* opts, float* V_inout, int
     stats->v_shift = h.mu;
     stats->status = h.status != 0 ? h.status : h.error;
     stats->path = -1;
+    int64_t b = mdp->n;
+    if (effective_batch(mdp, opts, &b) == RMB_OK) stats->batch = (int32_t)b;
     return stats->status;
 }
 

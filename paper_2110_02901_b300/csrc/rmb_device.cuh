@@ -189,8 +189,8 @@ struct GroupView {
     int size;   // CTAs in the group
 };
 
-// Bounded grid-wide barrier, split in two: grid_arrive() publishes this CTA's arrival (thread 0,
-// release add after a CTA barrier and a fence), grid_wait_arrived() spins with acquire loads until
+// Bounded grid-wide barrier, split in two: grid_arrive() publishes this CTA's arrival (a CTA barrier,
+// then one release add by thread 0), grid_wait_arrived() spins with acquire loads until
 // every CTA has arrived.  A wait gives up after timeout_ns, or as soon as another CTA reports an
 // error, and then returns false in every thread of the CTA.
 __device__ __forceinline__ void grid_arrive(Ctrl* c, unsigned long long& target, bool skip_arrive, int gsize)

@@ -13,6 +13,7 @@ from paper_2110_02901_b300 import build as rbuild
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "rmb.h")
+DIAG_HEADER = os.path.join(ROOT, "include", "rmb_diag.h")
 
 
 @pytest.fixture(scope="module")
@@ -21,8 +22,8 @@ def L():
     return rmb.lib()
 
 
-def declared_functions():
-    src = open(HEADER).read()
+def declared_functions(header=HEADER):
+    src = open(header).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(rmb_[a-z_]+)\s*\(", src)))
 
@@ -37,10 +38,19 @@ def test_header_declares_the_boundary():
 def test_every_declared_symbol_is_exported(L):
     out = subprocess.run(["nm", "-D", "--defined-only", rmb.LIB_PATH], capture_output=True, text=True, check=True).stdout
     exported = set(re.findall(r" T (rmb_\w+)", out))
-    missing = [f for f in declared_functions() if f not in exported]
+    declared = declared_functions() + declared_functions(DIAG_HEADER)
+    missing = [f for f in declared if f not in exported]
     assert not missing, missing
-    for f in declared_functions():
+    for f in declared:
         assert hasattr(L, f)
+
+
+def test_diagnostics_stay_out_of_the_boundary():
+    """The gather-rate probes are measurement tools, declared in rmb_diag.h only."""
+    diag = declared_functions(DIAG_HEADER)
+    assert diag == ["rmb_diag_gather_probe", "rmb_diag_gather_probe_tma"]
+    assert not set(diag) & set(declared_functions())
+    assert all(not f.startswith("rmb_diag_") for f in declared_functions())
 
 
 def test_struct_layouts_match_header():
@@ -236,7 +246,7 @@ def test_device_mdp_refuses_unreadable_tensors():
 
 def test_gather_probe_tma_arguments(L):
     """Argument checks of the gather4 probe, taken before any device work."""
-    f = L.rmb_gather_probe_tma
+    f = L.rmb_diag_gather_probe_tma
     f.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p,
                   ctypes.c_void_p]
     f.restype = ctypes.c_int
@@ -246,3 +256,47 @@ def test_gather_probe_tma_arguments(L):
     assert f(4100, 1000, 8192, 1024, 1, 4096, None) == rmb.RMB_ERR_ARG      # src not 16-byte aligned
     assert f(4096, 1000, 8192, 1024, 0, 4096, None) == rmb.RMB_ERR_ARG      # reps < 1
     assert f(None, 1000, 8192, 1024, 1, 4096, None) == rmb.RMB_ERR_ARG
+
+
+def test_noalloc_rejects_problems_beyond_the_fixed_scratch(L):
+    """rmb_vi_noalloc checks the scratch its solve needs on the host, before any CUDA call."""
+    n = 1 << 20                          # needs 8n + 16n bytes of scratch at b = n: 24 MiB > 8 MiB
+    d = rmb.rmb_mdp()
+    d.n, d.m, d.gamma, d.format = n, 8, 0.99, rmb.RMB_CSR
+    d.cost = d.row_ptr = d.col = d.prob = 4096   # never dereferenced: rejected on the host
+    o = rmb.Opts(batch=n).desc()
+    f = L.rmb_vi_noalloc
+    f.argtypes = [ctypes.POINTER(rmb.rmb_mdp), ctypes.POINTER(rmb.rmb_opts), ctypes.c_void_p, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.POINTER(rmb.rmb_stats), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(ctypes.byref(d), ctypes.byref(o), 4096, None, None, None, None) == rmb.RMB_ERR_TOO_LARGE
+    d.n = 400000                         # 12n bytes at b = 4096 (fits); draws add 16n of batch marks
+    o = rmb.Opts(batch=4096).desc()
+    assert L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(o)) <= 8 << 20
+    o = rmb.Opts(batch=4096, select=rmb.RMB_SELECT_UNIFORM).desc()
+    assert f(ctypes.byref(d), ctypes.byref(o), 4096, None, None, None, None) == rmb.RMB_ERR_TOO_LARGE
+    assert "no-allocation" in rmb.rmb_status_string(rmb.RMB_ERR_TOO_LARGE)
+
+
+def test_prioritized_arguments(L):
+    """rmb_vi_prioritized rejects bad arguments on the host."""
+    d = _fake_mdp()
+    f = L.rmb_vi_prioritized
+    f.argtypes = [ctypes.POINTER(rmb.rmb_mdp), ctypes.POINTER(rmb.rmb_opts), ctypes.c_int32, ctypes.c_float,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                  ctypes.POINTER(rmb.rmb_stats), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    g = L.rmb_vi_prioritized_workspace_bytes
+    g.argtypes = [ctypes.POINTER(rmb.rmb_mdp), ctypes.POINTER(rmb.rmb_opts)]
+    g.restype = ctypes.c_size_t
+    o = rmb.Opts(batch=10).desc()
+    need = g(ctypes.byref(d), ctypes.byref(o))
+    wo = rmb.Opts(batch=10, select=rmb.RMB_SELECT_WEIGHTED).desc()
+    assert need > L.rmb_workspace_bytes(ctypes.byref(d), ctypes.byref(wo)) + 4 * d.n
+    call = lambda refresh, frac, ws_bytes, V=4096, ws=1 << 20: f(ctypes.byref(d), ctypes.byref(o), refresh, frac, V,
+                                                                   None, None, ws, ws_bytes, None, None)
+    assert call(0, 0.05, need) == rmb.RMB_ERR_ARG                  # refresh < 1
+    assert call(4, 1.5, need) == rmb.RMB_ERR_ARG                   # floor_frac outside [0, 1]
+    assert call(4, 0.05, need, V=None) == rmb.RMB_ERR_ARG          # no values
+    assert call(4, 0.05, need - 1) == rmb.RMB_ERR_WORKSPACE        # workspace too small
+    assert call(4, 0.05, need, ws=(1 << 20) + 8) == rmb.RMB_ERR_WORKSPACE   # not 256-byte aligned

@@ -15,7 +15,7 @@ def test_gather_probe_checksum():
     g = torch.Generator(device="cuda").manual_seed(1)
     src = torch.rand(100000, device="cuda", generator=g)
     idx = torch.randint(0, 100000, (1 << 20,), dtype=torch.int32, device="cuda", generator=g)
-    out = rmb.rmb_gather_probe(src, idx, reps=3)
+    out = rmb.rmb_diag_gather_probe(src, idx, reps=3)
     want = 3 * src.double()[idx.long()].sum().item()
     assert abs(out.double().sum().item() - want) <= 1e-5 * abs(want)
 
@@ -30,7 +30,7 @@ def test_gather4_probe_checksum():
     src = torch.rand(100000, device="cuda", generator=g)
     idx = torch.randint(0, 100000, (1 << 20,), dtype=torch.int32, device="cuda", generator=g)
     idx[:8] = torch.tensor([0, 1, 2, 3, 99996, 99997, 99998, 99999], dtype=torch.int32, device="cuda")
-    out = rmb.rmb_gather_probe_tma(src, idx, reps=3)
+    out = rmb.rmb_diag_gather_probe_tma(src, idx, reps=3)
     assert torch.isfinite(out).all()
     want = 3 * src.double()[idx.long()].sum().item()
     assert abs(out.double().sum().item() - want) <= 1e-5 * abs(want)

@@ -192,6 +192,29 @@ def test_prioritized_vi_reaches_the_optimum():
     close(V.cpu().numpy(), jstar)
 
 
+def test_prioritized_entry_point_equals_its_rounds():
+    """rmb_vi_prioritized is the loop of rounds {residual weights; <= refresh weighted sweeps}: the same
+    rounds run one by one through rmb_residual_weights and rmb_vi give the same values bit for bit."""
+    mdp = mdpgen.maze(30, 800, gamma=0.95, slip=0.2, seed=4)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    st = rmb.rmb_vi_prioritized(dm, rmb.Opts(batch=50, seed=21, eps=1e-6, max_sweeps=100000, validate=False), V,
+                                refresh=3, floor_frac=0.1)
+    assert st["status"] == rmb.RMB_OK and st["iters"] >= 2
+    U = torch.zeros_like(V)
+    sweeps, rounds = 0, 0
+    while True:
+        w = rmb.rmb_residual_weights(dm, U, 0.1)
+        r = rmb.rmb_vi(dm, rmb.Opts(batch=50, seed=21, eps=1e-6, max_sweeps=3, start_sweep=sweeps, validate=False,
+                                    select=rmb.RMB_SELECT_WEIGHTED, weights=w), U)
+        sweeps += r["sweeps"]
+        rounds += 1
+        if r["status"] == rmb.RMB_OK:
+            break
+    assert (sweeps, rounds) == (st["sweeps"], st["iters"])
+    assert torch.equal(U, V)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 37])
 def test_tiny_problems_with_draws_and_stop_tests(n):
     mdp = mdpgen.csr_ragged(n, 3, 3, gamma=0.9, seed=n)

@@ -38,9 +38,10 @@ def _close(a, b):
     assert float(np.abs(a - b).max()) <= RTOL * scale
 
 
-def _solve_both(mdp, b, seed):
+def _solve_both(mdp, b, seed, select=rmb.RMB_SELECT_PERMUTATION, weights=None):
     dm = rmb.DeviceMDP.from_host(mdp)
-    opts = rmb.Opts(batch=b, seed=seed, eps=1e-6, max_sweeps=20000)
+    w = None if weights is None else torch.as_tensor(weights, dtype=torch.int32, device="cuda")
+    opts = rmb.Opts(batch=b, seed=seed, eps=1e-6, max_sweeps=20000, select=select, weights=w)
     V_ref = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
     pi_ref = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
     gap_ref = torch.empty(mdp.n, dtype=torch.float32, device="cuda")
@@ -51,6 +52,7 @@ def _solve_both(mdp, b, seed):
     st = rmb.rmb_vi_noalloc(dm, opts, V, pi, gap)
     assert st["status"] == rmb.RMB_OK == st_ref["status"]
     assert st["sweeps"] == st_ref["sweeps"]
+    assert st["batch"] == st_ref["batch"] == min(b, mdp.n)
     _close(V, V_ref)
     clear = gap_ref > 1e-6 * max(1.0, float(V_ref.abs().max()))
     assert torch.equal(pi[clear], pi_ref[clear])
@@ -63,15 +65,33 @@ def test_noalloc_matches_rmb_vi_on_consecutive_calls():
     _solve_both(mdpgen.dense_dirichlet(500, 4, gamma=0.95, seed=0), 50, 12345)
 
 
-def test_noalloc_rejects_problems_beyond_the_fixed_scratch():
-    n = 1 << 20                          # needs 8n + 16n bytes of scratch at b = n: 24 MiB > 8 MiB
-    d = rmb.rmb_mdp()
-    d.n, d.m, d.gamma, d.format = n, 8, 0.99, rmb.RMB_CSR
-    d.cost = d.row_ptr = d.col = d.prob = 4096   # never dereferenced: rejected on the host
-    o = rmb.Opts(batch=n).desc()
-    f = rmb.lib().rmb_vi_noalloc
-    f.argtypes = [ctypes.POINTER(rmb.rmb_mdp), ctypes.POINTER(rmb.rmb_opts), ctypes.c_void_p, ctypes.c_void_p,
-                  ctypes.c_void_p, ctypes.POINTER(rmb.rmb_stats), ctypes.c_void_p]
-    f.restype = ctypes.c_int
-    assert f(ctypes.byref(d), ctypes.byref(o), 4096, None, None, None, None) == rmb.RMB_ERR_TOO_LARGE
-    assert "no-allocation" in rmb.rmb_status_string(rmb.RMB_ERR_TOO_LARGE)
+def test_noalloc_draws_clear_the_shared_scratch():
+    """Draws with replacement keep per-state batch marks (and, with weights, cumulative weights) in
+    the scratch array; a call must not see the stamps of the call before it.  Two uniform and two
+    weighted solves back to back, each against rmb_vi with its own fresh workspace."""
+    mdp = mdpgen.csr_uniform_k(6000, 4, 16, gamma=0.95, seed=3)
+    _solve_both(mdp, 500, 11, select=rmb.RMB_SELECT_UNIFORM)
+    _solve_both(mdp, 500, 11, select=rmb.RMB_SELECT_UNIFORM)
+    wts = np.random.default_rng(5).integers(1, 1000, mdp.n)
+    _solve_both(mdp, 700, 13, select=rmb.RMB_SELECT_WEIGHTED, weights=wts)
+    _solve_both(mdp, 700, 13, select=rmb.RMB_SELECT_WEIGHTED, weights=wts)
+
+
+def test_noalloc_allocates_no_device_memory():
+    """Once its set-up has run, a call takes no device memory: the free memory the driver reports is
+    the same before and after a solve (torch's caching allocator is not involved in the call)."""
+    mdp = mdpgen.csr_uniform_k(5000, 8, 32, gamma=0.99, seed=4)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    opts = rmb.Opts(batch=256, seed=1, eps=1e-6, max_sweeps=20000)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
+    rmb.rmb_vi_noalloc(dm, opts, V, pi)          # set-up: the scratch address is looked up once
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        V.zero_()
+        st = rmb.rmb_vi_noalloc(dm, opts, V, pi, stats=False)
+        assert st is None
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
