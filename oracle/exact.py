@@ -7,6 +7,9 @@
   enumeration on tiny problems (m^n policies).
 * ``policy_iteration``: exact PI (Sec. II-C) with direct solves, ending when the greedy policy of
   J_mu is mu itself; its result is certified by one Bellman pass (J = TJ, eq. (5)).
+* ``dense_policy_iteration``: the same PI for dense transition rows that are too large to hold in
+  host memory at once (they are read in row chunks from a caller-supplied accessor); the policy
+  solve is a dense LU of (I - alpha P_mu) and every Bellman pass streams all rows once.
 
 Everything here is numpy/scipy FP64 and is independent of ``oracle.c``.
 """
@@ -110,6 +113,55 @@ def policy_iteration(mdp, max_iters: int = 200):
         new_pi = np.where(keep, pi, new_pi).astype(np.int32)
         if np.array_equal(new_pi, pi):
             return J, pi, float(np.max(np.abs(TJ - J)))
+        pi = new_pi
+    raise RuntimeError("policy iteration did not terminate")
+
+
+def dense_bellman_pass(rows_of, cost, gamma, J, n, m, chunk_states=512):
+    """One FP64 Bellman pass (eq. (7)) over dense rows read in chunks: rows_of(r0, r1) returns the
+    rows r0..r1-1 (row r = s*m + a, each of length n, any float dtype).  Returns (TJ, Q [n, m])."""
+    J = np.asarray(J, dtype=np.float64)
+    c = np.asarray(cost, dtype=np.float64).reshape(n, m)
+    Q = np.empty((n, m), dtype=np.float64)
+    for s0 in range(0, n, chunk_states):
+        s1 = min(n, s0 + chunk_states)
+        R = np.asarray(rows_of(s0 * m, s1 * m), dtype=np.float64).reshape((s1 - s0) * m, n)
+        Q[s0:s1] = c[s0:s1] + gamma * (R @ J).reshape(s1 - s0, m)
+    Q = np.where(np.isinf(c), np.inf, Q)
+    return Q.min(axis=1), Q
+
+
+def dense_policy_iteration(rows_of, rows_at, cost, gamma, n, m, pi0=None, chunk_states=512, max_iters=100):
+    """Exact policy iteration (Sec. II-C) for a dense MDP whose rows come from accessors:
+    rows_of(r0, r1) -> rows r0..r1-1 and rows_at(idx) -> the rows with the given indices.
+    Evaluation: J_mu = (I - alpha P_mu)^{-1} g_mu by a dense LU (eq. (4)); improvement: the greedy
+    policy of J_mu, keeping the current action where it ties the minimum up to the rounding of the
+    solve.  Ends when the policy repeats; then T J = J (eq. (5)) certifies J = J*.
+    Returns dict(J, pi, resid = ||TJ - J||_inf, gap = second smallest minus smallest Q, iters)."""
+    c = np.asarray(cost, dtype=np.float64).reshape(n, m)
+    if pi0 is None:
+        pi = np.argmin(np.where(np.isinf(c), np.inf, c), axis=1).astype(np.int64)
+    else:
+        pi = np.asarray(pi0, dtype=np.int64).copy()
+    states = np.arange(n, dtype=np.int64)
+    for it in range(1, max_iters + 1):
+        g = c[states, pi]
+        if np.isinf(g).any():
+            raise ValueError("policy uses an inadmissible action")
+        A = np.asarray(rows_at(states * m + pi), dtype=np.float64).reshape(n, n)
+        A *= -gamma
+        A[states, states] += 1.0
+        J = np.linalg.solve(A, g)
+        del A
+        TJ, Q = dense_bellman_pass(rows_of, cost, gamma, J, n, m, chunk_states)
+        tie = 1e-11 * max(1.0, float(np.max(np.abs(J))))
+        keep = Q[states, pi] <= TJ + tie
+        new_pi = np.where(keep, pi, np.argmin(Q, axis=1))
+        if np.array_equal(new_pi, pi):
+            part = np.sort(Q, axis=1)
+            gap = part[:, 1] - part[:, 0] if m > 1 else np.full(n, np.inf)
+            return {"J": J, "pi": pi.astype(np.int32), "resid": float(np.max(np.abs(TJ - J))), "gap": gap,
+                    "iters": it}
         pi = new_pi
     raise RuntimeError("policy iteration did not terminate")
 

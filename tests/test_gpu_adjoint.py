@@ -82,15 +82,16 @@ def test_gradient_matches_direct_solve(n, m, k, g, b):
     close(gz_g.cpu().numpy(), gz, GTOL)
 
 
-def test_gradient_matches_central_differences():
-    """64 coordinates: 32 logits of greedy rows, 16 costs of greedy actions, 16 uniform costs."""
-    n = 4096
-    mdp = mdpgen.csr_uniform_k(n, 8, 16, gamma=0.95, seed=4, prob_kind="softmax")
-    dm, z, V, pi, gap = gpu_forward(mdp)
+def _central_differences(mdp, b, w_seed):
+    """64 coordinates: 32 logits of greedy rows, 16 costs of greedy actions, 16 uniform costs (kept
+    where the state's Q-gap exceeds 1e-3, so the optimal policy is the same at +-h); each compared
+    with (L(theta + h) - L(theta - h)) / 2h, L = w . J_pi* from FP64 solves of the perturbed MDP."""
+    n = mdp.n
+    dm, z, V, pi, gap = gpu_forward(mdp, b=b)
     pi_h = pi.cpu().numpy()
-    w = mdpgen.random_values(n, seed=11).astype(np.float64)
+    w = mdpgen.random_values(n, seed=w_seed).astype(np.float64)
     wt = torch.from_numpy(w.astype(np.float32)).cuda()
-    _, gc_g, gz_g, _ = rmb.rmb_fixed_point_grad(dm, pi, V, wt, rmb.Opts(batch=256, seed=3, eps=1e-7, max_sweeps=100000))
+    _, gc_g, gz_g, _ = rmb.rmb_fixed_point_grad(dm, pi, V, wt, rmb.Opts(batch=b, seed=3, eps=1e-7, max_sweeps=100000))
     gc_g, gz_g = gc_g.cpu().numpy().astype(np.float64), gz_g.cpu().numpy().astype(np.float64)
     z0 = mdp.logits.astype(np.float64)
     base = dataclasses.replace(mdp)
@@ -102,6 +103,7 @@ def test_gradient_matches_central_differences():
     h = 1e-4
     rng = np.random.default_rng(0)
     ok_states = np.nonzero(jgap > 1e-3)[0]
+    k = mdp.k_uniform
 
     def L_of(mod):
         return float(w @ exact.policy_value(mod, pistar))
@@ -109,7 +111,7 @@ def test_gradient_matches_central_differences():
     coords = []
     for s in rng.choice(ok_states, 32, replace=False):
         r = s * mdp.m + pistar[s]
-        coords.append(("z", int(mdp.row_ptr[r]) + int(rng.integers(0, 16))))
+        coords.append(("z", int(mdp.row_ptr[r]) + int(rng.integers(0, k))))
     for s in rng.choice(ok_states, 16, replace=False):
         coords.append(("c", int(s * mdp.m + pistar[s])))
     for r in rng.integers(0, n * mdp.m, 16):
@@ -132,6 +134,17 @@ def test_gradient_matches_central_differences():
             got = gz_g[i]
         fd = (L_of(mp) - L_of(mm)) / (2 * h)
         assert abs(got - fd) <= GTOL * gmax, (kind, i, got, fd)
+
+
+def test_gradient_matches_central_differences():
+    mdp = mdpgen.csr_uniform_k(4096, 8, 16, gamma=0.95, seed=4, prob_kind="softmax")
+    _central_differences(mdp, 256, 11)
+
+
+def test_gradient_matches_central_differences_full_size():
+    """The differentiable fixed point at full size (n = 65536, m = 8, k = 16, gamma = 0.95) in the
+    bench's launch configuration (b = 16384 for the forward and the adjoint solve)."""
+    _central_differences(mdpgen.config5(), 16384, 13)
 
 
 def test_autograd_function_and_full_size_config():

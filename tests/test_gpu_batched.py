@@ -106,10 +106,11 @@ def test_batched_fixed_batch_sizes_are_respected():
         assert np.max(np.abs(v - ref["V"])) <= 1e-5 * max(1.0, np.abs(ref["V"]).max())
 
 
-def test_batched_full_config_sampled_against_oracle():
+def test_batched_full_config_against_single_solves_and_oracle():
     """The bench's batched workload at full size (256 MDPs, n log-uniform in [256, 65536], m in 2..16,
-    k = 16) in one launch with the autotuned plan; every MDP converges, and 8 sampled MDPs equal the
-    FP64 oracle's MB-VI at their planned b."""
+    k = 16) in one launch with the autotuned plan: every MDP converges; every MDP's values, policy and
+    sweep count equal a single rmb_vi solve at its planned b bit for bit; and 64 MDPs, every fourth
+    by size, equal the FP64 oracle's MB-VI at their planned b."""
     mdps = mdpgen.config3()
     opts = rmb.Opts(batch=1, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000)
     dms, Vs, pis, B = _run_batch(mdps, opts)
@@ -117,8 +118,16 @@ def test_batched_full_config_sampled_against_oracle():
     res = B.results()
     plan = B.plan_table()
     assert all(r["status"] == rmb.RMB_OK for r in res)
-    rng = np.random.default_rng(5)
-    for i in sorted(rng.choice(len(mdps), size=8, replace=False)):
+    for i, dm in enumerate(dms):
+        V1 = torch.zeros(mdps[i].n, dtype=torch.float32, device="cuda")
+        pi1 = torch.empty(mdps[i].n, dtype=torch.int32, device="cuda")
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=plan[i]["batch"], seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000,
+                                     validate=False), V1, pi1)
+        assert st["sweeps"] == res[i]["sweeps"], i
+        assert torch.equal(V1, Vs[i]), i
+        assert torch.equal(pi1, pis[i]), i
+    by_size = np.argsort([m.n for m in mdps], kind="stable")
+    for i in by_size[::4]:
         ref = oracle.mbvi(mdps[i], plan[i]["batch"], seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000)
         v = Vs[i].cpu().numpy().astype(np.float64)
         assert np.max(np.abs(v - ref["V"])) <= 1e-5 * max(1.0, np.abs(ref["V"]).max()), i

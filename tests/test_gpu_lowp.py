@@ -11,6 +11,7 @@ import pytest
 
 import mdpgen
 import oracle
+from oracle import exact
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -131,7 +132,8 @@ def test_converged_lowp_and_refined_solutions(dt):
 
 def test_refined_solve_with_model_batch():
     """batch = 0 in rmb_vi_refined: one b (the model's, for the float32 rows) for both solves, in the
-    workspace sized for the float32 MDP."""
+    workspace sized for the float32 MDP.  The result equals the oracle's two phases at the same sweep
+    counts: MB-VI on the decoded fp8 rows, then MB-VI on the float32 rows from there."""
     n = 2048
     mdp = mdpgen.dense_dirichlet(n, 8, alpha=0.1, gamma=0.99, seed=7, cost_dist="normal")
     dm = rmb.DeviceMDP.from_host(mdp)
@@ -139,8 +141,11 @@ def test_refined_solve_with_model_batch():
     V = torch.zeros(n, dtype=torch.float32, device="cuda")
     s1, s2 = rmb.rmb_vi_refined(lp, dm, rmb.Opts(batch=0, seed=5, eps=1e-6, max_sweeps=100000), 1e-6, V)
     assert s2["status"] == rmb.RMB_OK and s1["batch"] == s2["batch"] >= 1
-    ref = oracle.mbvi(mdp, s2["batch"], seed=5, eps=1e-7, max_sweeps=100000)
-    close(V.cpu().numpy(), ref["V"], tol=2e-5)
+    b = s2["batch"]
+    codes, _ = cpu_codes(mdp.P.reshape(-1, n), rmb.RMB_P_FP8E4M3)
+    ref1 = oracle.mbvi(decoded_mdp(mdp, codes), b, seed=5, eps=0.0, max_sweeps=s1["sweeps"])
+    ref2 = oracle.mbvi(mdp, b, seed=5, eps=0.0, max_sweeps=s2["sweeps"], V0=ref1["V"])
+    close(V.cpu().numpy(), ref2["V"])
 
 
 def _rows_only_mdp(n, m, gamma, s, rows, cost_s):
@@ -191,3 +196,47 @@ def test_dense_config4_full_size_sampled(dt):
         mdp = _rows_only_mdp(n, m, g, int(s), R, costs[s])
         want = min(oracle.q_factor(mdp, int(s), a, V0.astype(np.float64)) for a in range(m))
         assert abs(v1[s] - want) <= 1e-5 * max(1.0, abs(want)), (s, v1[s], want)
+
+
+def test_dense_config4_full_size_certified():
+    """The dense workload at full size (n = 16384, m = 16, Dirichlet(0.1) rows, N(0,1) costs,
+    gamma = 0.999, P drawn on the device) in the bench's launch configuration (b = 4096), solved to a
+    sweep residual of 1e-6 with float32 rows, with bf16 codes + float32 refinement and with fp8 codes +
+    float32 refinement.  The FP64 oracle solves the same MDP exactly: policy iteration from the greedy
+    policy of the costs, each policy value by a dense LU of (I - gamma P_pi), each improvement by a
+    Bellman pass over all 17 GB of rows streamed to the host in chunks, until the policy repeats; then
+    T J = J (eq. (5)) certifies J = J*.  Every storage type's values must equal J* within 1e-5 of
+    ||J*||_inf and its greedy policy must be the optimal one wherever J*'s Q-gap is clear."""
+    n, m, b, g = 16384, 16, 4096, 0.999
+    P, cost = mdpgen.dense_dirichlet_device(n, m, 0.1, g, seed=3)
+    d32 = rmb.DeviceMDP(n, m, g, "dense", cost, P=P.reshape(-1))
+    opts = rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000, validate=False)
+    out = {}
+    V = torch.zeros(n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(n, dtype=torch.int32, device="cuda")
+    st = rmb.rmb_vi(d32, opts, V, pi)
+    assert st["status"] == rmb.RMB_OK and st["path"] == "dense-tma"
+    out["f32"] = (V.cpu().numpy().astype(np.float64), pi.cpu().numpy())
+    for name, dt in (("bf16", rmb.RMB_P_BF16), ("fp8", rmb.RMB_P_FP8E4M3)):
+        lp = rmb.dense_lowp(d32, dt)
+        V.zero_()
+        s1, s2 = rmb.rmb_vi_refined(lp, d32, opts, 1e-6, V, pi)
+        assert s1["status"] == rmb.RMB_OK and s2["status"] == rmb.RMB_OK
+        out[name] = (V.cpu().numpy().astype(np.float64), pi.cpu().numpy())
+        del lp
+    rows = P.reshape(n * m, n)
+    cert = exact.dense_policy_iteration(lambda r0, r1: rows[r0:r1].cpu().numpy(),
+                                        lambda idx: rows[torch.from_numpy(np.asarray(idx)).cuda()].cpu().numpy(),
+                                        cost.cpu().numpy(), g, n, m, chunk_states=256)
+    jstar = cert["J"]
+    scale = max(1.0, float(np.abs(jstar).max()))
+    # the certificate: ||T J - J||_inf at FP64 rounding level, so ||J - J*|| <= resid / (1 - gamma) is tiny
+    assert cert["resid"] / (1 - g) <= 1e-8 * scale, cert["resid"]
+    clear = cert["gap"] > 1e-6 * scale
+    assert clear.mean() > 0.99
+    for name, (v, p) in out.items():
+        err = float(np.abs(v - jstar).max())
+        print(f"dense n=16384 {name}: sup-norm error vs certified J* {err:.3e} (relative {err / scale:.2e}), "
+              f"policy iterations {cert['iters']}")
+        assert err <= RTOL * scale, (name, err, scale)
+        assert np.array_equal(p[clear], cert["pi"][clear]), name

@@ -403,10 +403,10 @@ def test_batch_zero_uses_the_time_model_choice(make):
 
 def test_csr_headline_config_full_size():
     """The bench's workload at full size (n = 2^20, m = 8, k = 32, gamma = 0.99) in its launch
-    configuration (b = 262144): the whole value vector after 3 sweeps equals the FP64 oracle's; the
-    converged solve (sweep residual 1e-6) has a small FP64 Bellman residual ||TV - V||_inf at the GPU's
-    values, hence a certified error bound, and its greedy policy is the oracle's arg-min at those values
-    wherever the Q-gap is clear."""
+    configuration (b = 262144): the whole value vector after 3 sweeps, and the converged solve (sweep
+    residual 1e-6), against the FP64 oracle's MB-VI element by element (the GPU trajectory is taken at
+    the oracle's stopping sweep), and the greedy policy against the oracle's wherever its Q-gap is
+    clear."""
     mdp = mdpgen.config2()
     dm = rmb.DeviceMDP.from_host(mdp)
     b = 262144
@@ -414,15 +414,19 @@ def test_csr_headline_config_full_size():
     rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=3, validate=False), V)
     ref = oracle.mbvi(mdp, b, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=3)
     close(V.cpu().numpy(), ref["V"])
+    ref = oracle.mbvi(mdp, b, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=5000)
+    k = ref["sweeps"]
     V.zero_()
     pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
     st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000, validate=False), V, pi)
     assert st["status"] == rmb.RMB_OK
-    v = V.cpu().numpy().astype(np.float64)
-    TV, gpi, gap, resid = oracle.greedy(mdp, v)
-    assert resid <= 5e-6
-    g = mdp.gamma
-    assert g / (1 - g) * resid <= 5e-4          # ||V - J*||_inf bound from the FP64 Bellman residual
-    sel = gap > 1e-6 * max(1.0, float(np.abs(v).max()))
+    # the float32 and FP64 sweep changes cross 1e-6 within a sweep or two of each other
+    assert abs(st["sweeps"] - k) <= 2, (st["sweeps"], k)
+    if st["sweeps"] != k:
+        V.zero_()
+        rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=k, validate=False), V, pi)
+    close(V.cpu().numpy(), ref["V"])
+    _, opi, ogap, _ = oracle.greedy(mdp, ref["V"])
+    sel = ogap > 1e-6 * max(1.0, float(np.abs(ref["V"]).max()))
     assert sel.mean() > 0.99
-    assert np.array_equal(pi.cpu().numpy()[sel], gpi[sel])
+    assert np.array_equal(pi.cpu().numpy()[sel], opi[sel])

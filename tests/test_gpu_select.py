@@ -230,11 +230,15 @@ def test_tiny_problems_with_draws_and_stop_tests(n):
                                     weights=dev_w(w) if select == 2 else None), V)
             close(V.cpu().numpy(), ref["V"])
         for rk in (0, 1):
+            # both stop tests end the solve; values are compared at the oracle's stopping sweep (the
+            # float32 and FP64 residuals may cross eps a sweep apart)
             ref = oracle.mbvi(mdp, b, 3, eps=1e-6, max_sweeps=10000, V0=V0, residual_kind=rk)
             V = torch.from_numpy(V0).cuda()
             st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=3, eps=1e-6, max_sweeps=10000, residual_kind=rk), V)
-            assert st["status"] == rmb.RMB_OK
-            close(V.cpu().numpy(), ref["V"], tol=2e-5)
+            assert st["status"] == rmb.RMB_OK and abs(st["sweeps"] - ref["sweeps"]) <= 2
+            V = torch.from_numpy(V0).cuda()
+            rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=3, eps=0.0, max_sweeps=ref["sweeps"]), V)
+            close(V.cpu().numpy(), ref["V"])
     jstar, _, _ = exact.policy_iteration(mdp)
     V = torch.zeros(n, dtype=torch.float32, device="cuda")
     st = rmb.rmb_vi(dm, rmb.Opts(batch=1, eps=1e-7, max_sweeps=100000, flags=rmb.RMB_FLAG_ASYNC), V)

@@ -513,3 +513,55 @@ def test_bellman_residual_stop_rule():
         # the sweep-change rule can stop with a larger full residual; the trajectories agree up to there
         assert np.array_equal(r1["deltas"][:r0["sweeps"]], r0["deltas"])
         assert full0 >= 0.0
+
+
+# ------------------------------------------------------------------------------------------------
+# The dense certificate (exact policy iteration over rows read in chunks), used at n = 16384 where
+# the transition rows (17 GB) never sit in host memory at once.
+def _dense_accessors(mdp):
+    R = mdp.P.reshape(mdp.n * mdp.m, mdp.n)
+    return (lambda r0, r1: R[r0:r1]), (lambda idx: R[np.asarray(idx)])
+
+
+def _peaked_tiny(seed):
+    # the n = 16384 recipe in miniature: Dirichlet(0.1) rows, N(0,1) costs, gamma = 0.999
+    return mdpgen.dense_dirichlet(6, 3, alpha=0.1, gamma=0.999, seed=40 + seed, cost_dist="normal")
+
+
+def test_dense_policy_iteration_matches_brute_force(ex=exact):
+    for seed in range(4):
+        mdp = _peaked_tiny(seed)
+        rows_of, rows_at = _dense_accessors(mdp)
+        jstar = exact.brute_force(mdp)
+        for chunk in (1, 4, 6):
+            r = ex.dense_policy_iteration(rows_of, rows_at, mdp.cost, mdp.gamma, mdp.n, mdp.m, chunk_states=chunk)
+            assert np.max(np.abs(r["J"] - jstar)) <= 1e-9 * np.abs(jstar).max(), (seed, chunk)
+            assert r["resid"] <= 1e-10 * np.abs(jstar).max()
+            J_pi = exact.policy_value(mdp, r["pi"])
+            assert np.max(np.abs(J_pi - jstar)) <= 1e-9 * np.abs(jstar).max()
+
+
+def test_dense_policy_iteration_matches_converged_mbvi(ex=exact):
+    """Against the C oracle's MB-VI run to its FP64 floor (independent code), from any start policy."""
+    mdp = mdpgen.dense_dirichlet(300, 5, alpha=0.1, gamma=0.99, seed=12, cost_dist="normal")
+    rows_of, rows_at = _dense_accessors(mdp)
+    ref = oracle.mbvi(mdp, mdp.n, seed=1, eps=1e-12, max_sweeps=100000)
+    scale = np.abs(ref["V"]).max()
+    _, pi_ref, gap_ref, _ = oracle.greedy(mdp, ref["V"])
+    for pi0 in (None, np.random.default_rng(3).integers(0, mdp.m, mdp.n)):
+        r = ex.dense_policy_iteration(rows_of, rows_at, mdp.cost, mdp.gamma, mdp.n, mdp.m, pi0=pi0, chunk_states=37)
+        assert np.max(np.abs(r["J"] - ref["V"])) <= 1e-9 * scale
+        clear = gap_ref > 1e-8 * scale
+        assert np.array_equal(r["pi"][clear], pi_ref[clear])
+        assert np.allclose(r["gap"][clear], gap_ref[clear], rtol=1e-6, atol=1e-8 * scale)
+
+
+def test_dense_bellman_pass_matches_the_oracle(ex=exact):
+    mdp = mdpgen.dense_dirichlet(50, 4, alpha=0.1, gamma=0.999, seed=13, cost_dist="normal")
+    rows_of, _ = _dense_accessors(mdp)
+    J = mdpgen.random_values(mdp.n, seed=2).astype(np.float64) * 30
+    TJ_ref, _, _, _ = oracle.greedy(mdp, J)
+    for chunk in (1, 7, 50):
+        TJ, Q = ex.dense_bellman_pass(rows_of, mdp.cost, mdp.gamma, J, mdp.n, mdp.m, chunk)
+        assert np.max(np.abs(TJ - TJ_ref)) <= 1e-12 * np.abs(TJ_ref).max()
+        assert np.max(np.abs(Q[7] - [oracle.q_factor(mdp, 7, a, J) for a in range(mdp.m)])) <= 1e-12 * 100

@@ -8,6 +8,7 @@ import shutil
 import subprocess
 import tempfile
 
+import numpy as np
 import pytest
 
 import oracle
@@ -102,4 +103,48 @@ def test_pins_catch_planted_mistake(name, monkeypatch):
         assert caught, f"no pin caught the planted mistake {name}"
     finally:
         oracle._BOUND_CACHE.clear()
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
+# Planted mistakes in a copy of exact.py's dense certificate (the FP64 policy iteration used on the
+# n = 16384 dense workload), each caught by one of its pins.
+EXACT_MUTANTS = {
+    "dense_pass_drops_discount": ("Q[s0:s1] = c[s0:s1] + gamma * (R @ J).reshape(s1 - s0, m)",
+                                  "Q[s0:s1] = c[s0:s1] + (R @ J).reshape(s1 - s0, m)"),
+    "dense_pass_wrong_chunk_rows": ("R = np.asarray(rows_of(s0 * m, s1 * m), dtype=np.float64)",
+                                    "R = np.asarray(rows_of(s0, s1 * m - s0 * (m - 1)), dtype=np.float64)"),
+    "policy_solve_transposed": ("        J = np.linalg.solve(A, g)\n        del A",
+                                "        J = np.linalg.solve(A.T, g)\n        del A"),
+    "policy_rows_of_the_wrong_action": ("A = np.asarray(rows_at(states * m + pi), dtype=np.float64)",
+                                        "A = np.asarray(rows_at(states * m + (pi + 1) % m), dtype=np.float64)"),
+    "improvement_takes_the_maximum": ("new_pi = np.where(keep, pi, np.argmin(Q, axis=1))",
+                                      "new_pi = np.where(keep, pi, np.argmax(Q, axis=1))"),
+}
+
+EXACT_PINS = [T.test_dense_policy_iteration_matches_brute_force, T.test_dense_policy_iteration_matches_converged_mbvi,
+              T.test_dense_bellman_pass_matches_the_oracle]
+
+
+@pytest.mark.parametrize("name", sorted(EXACT_MUTANTS))
+def test_pins_catch_planted_mistake_in_the_dense_certificate(name):
+    import importlib.util
+    old, new = EXACT_MUTANTS[name]
+    src = open(os.path.join(os.path.dirname(obuild.__file__), "exact.py")).read()
+    assert src.count(old) == 1, old
+    tmp = tempfile.mkdtemp(prefix="exact_mut_")
+    try:
+        path = os.path.join(tmp, "exact_mut.py")
+        open(path, "w").write(src.replace(old, new))
+        spec = importlib.util.spec_from_file_location("exact_mut", path)
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        caught = False
+        for pin in EXACT_PINS:
+            try:
+                pin(ex=mod)
+            except (AssertionError, RuntimeError, ValueError, IndexError, np.linalg.LinAlgError):
+                caught = True
+                break
+        assert caught, f"no pin caught the planted mistake {name}"
+    finally:
         shutil.rmtree(tmp, ignore_errors=True)
