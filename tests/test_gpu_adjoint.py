@@ -103,7 +103,7 @@ def _central_differences(mdp, b, w_seed):
     h = 1e-4
     rng = np.random.default_rng(0)
     ok_states = np.nonzero(jgap > 1e-3)[0]
-    k = mdp.k_uniform
+    k = int(mdp.row_ptr[1] - mdp.row_ptr[0])      # uniform row length
 
     def L_of(mod):
         return float(w @ exact.policy_value(mod, pistar))

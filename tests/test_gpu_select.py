@@ -198,14 +198,15 @@ def test_prioritized_entry_point_equals_its_rounds():
     mdp = mdpgen.maze(30, 800, gamma=0.95, slip=0.2, seed=4)
     dm = rmb.DeviceMDP.from_host(mdp)
     V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
-    st = rmb.rmb_vi_prioritized(dm, rmb.Opts(batch=50, seed=21, eps=1e-6, max_sweeps=100000, validate=False), V,
+    # eps above the float32 floor of this maze (|V| ~ 20: ||TV - V||_inf settles at a few 1e-6 under draws)
+    st = rmb.rmb_vi_prioritized(dm, rmb.Opts(batch=50, seed=21, eps=1e-5, max_sweeps=100000, validate=False), V,
                                 refresh=3, floor_frac=0.1)
     assert st["status"] == rmb.RMB_OK and st["iters"] >= 2
     U = torch.zeros_like(V)
     sweeps, rounds = 0, 0
     while True:
         w = rmb.rmb_residual_weights(dm, U, 0.1)
-        r = rmb.rmb_vi(dm, rmb.Opts(batch=50, seed=21, eps=1e-6, max_sweeps=3, start_sweep=sweeps, validate=False,
+        r = rmb.rmb_vi(dm, rmb.Opts(batch=50, seed=21, eps=1e-5, max_sweeps=3, start_sweep=sweeps, validate=False,
                                     select=rmb.RMB_SELECT_WEIGHTED, weights=w), U)
         sweeps += r["sweeps"]
         rounds += 1
