@@ -236,6 +236,19 @@ int rmb_greedy(const rmb_mdp *mdp, const rmb_opts *opts, const float *V, float *
 int rmb_permutation(int64_t n, uint64_t seed, uint64_t sweep, int32_t *out, void *stream);
 
 /*
+ * One backup of an explicit list of states: W_out[i] = min_a c(s,a) + gamma sum_j P(j|s,a) V(j) with
+ * s = states[i] (eq. (7) restricted to the list), or, with pi != NULL, the policy's backup
+ * c(s,pi(s)) + gamma sum_j P(j|s,pi(s)) V(j) (T_pi of eq. (4)).  Float32 values as given (not
+ * centred), one warp per listed state.  This is the step one rank takes in a row-partitioned
+ * mini-batch sweep: the batch's states that it owns, read from its replica of V (eq. (11): every state
+ * of a batch reads the values before the batch).
+ *   V [n], states [count] int32 (entries outside [0,n) are clamped into it), pi [n] or NULL,
+ *   W_out [count]: device.  RMB_DENSE with coded rows returns RMB_ERR_UNSUPPORTED.  Asynchronous.
+ */
+int rmb_backup_states(const rmb_mdp *mdp, const float *V, const int32_t *states, int64_t count,
+                      const int32_t *pi, float *W_out, void *stream);
+
+/*
  * Device validation of an MDP: probabilities finite and in [0,1], |row sum - 1| <= 1e-4,
  * indices in [0,n), row_ptr non-decreasing from 0 (and == r*k when k_uniform is declared),
  * costs not NaN and not -inf, at least one admissible action per state.

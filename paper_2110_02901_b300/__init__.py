@@ -428,6 +428,24 @@ def rmb_vi_noalloc(mdp: DeviceMDP, opts: Opts, V, pi=None, qgap=None, stats: boo
     return _finish(st, s, "rmb_vi_noalloc") if check else (st, s.as_dict() if s is not None else None)
 
 
+def rmb_backup_states(mdp: DeviceMDP, V, states, pi=None, out=None, stream=None):
+    """W[i] = min_a Q(states[i], a) at V (or Q at pi[states[i]]); float32 CUDA tensors, states int32."""
+    import torch
+    _check(V, torch.float32, mdp.n, "V")
+    _check(states, torch.int32, 0, "states")
+    _check(pi, torch.int32, mdp.n, "pi")
+    out = torch.empty(states.numel(), dtype=torch.float32, device=V.device) if out is None else out
+    _check(out, torch.float32, states.numel(), "out")
+    f = lib().rmb_backup_states
+    f.argtypes = [ctypes.POINTER(rmb_mdp), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    st = f(ctypes.byref(mdp.desc), _ptr(V), _ptr(states), states.numel(), _ptr(pi), _ptr(out), _stream_handle(stream))
+    if st != RMB_OK:
+        raise RmbError(st, "rmb_backup_states")
+    return out
+
+
 def rmb_softmax_rows(mdp: DeviceMDP, logits, prob_out, stream=None):
     """prob_out = softmax of each (s,a) row of logits (CSR, uniform k)."""
     import torch

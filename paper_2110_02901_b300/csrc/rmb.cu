@@ -116,6 +116,57 @@ __global__ void rmb_tr_sort_kernel(int n, const int64_t* __restrict__ row_ptr, i
     }
 }
 
+// ------------------------------------------------------------------------------------------------
+// One backup of an explicit list of states (eq. (7) restricted to the list; with a policy, eq. (4)'s
+// T_pi): W[i] = min_a c(s,a) + gamma sum_j P(j|s,a) V(j) for s = states[i], one warp per listed state,
+// float32 values as given (not centred).  The step a rank of a row-partitioned batch takes for the
+// states it owns.
+// ------------------------------------------------------------------------------------------------
+struct BL {
+    int n, m, fmt;
+    const float* P;
+    const int64_t* row_ptr;
+    const int32_t* col;
+    const float* prob;
+    const float* cost;
+    float gamma;
+    const float* V;
+    const int32_t* states;
+    int64_t count;
+    const int32_t* pi;
+    float* W;
+};
+
+__global__ void rmb_backup_list_kernel(BL p)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint32_t nm1 = (uint32_t)(p.n - 1);
+    for (int64_t i = warp; i < p.count; i += nw) {
+        const int s = (int)min((uint32_t)p.states[i], nm1);
+        const int a0 = p.pi ? (int)min((uint32_t)p.pi[s], (uint32_t)(p.m - 1)) : 0;
+        const int a1 = p.pi ? a0 + 1 : p.m;
+        float best = kInf;
+        for (int a = a0; a < a1; ++a) {
+            const int64_t r = (int64_t)s * p.m + a;
+            float part = 0.f;
+            if (p.fmt == RMB_CSR) {
+                const int64_t e0 = p.row_ptr[r], e1 = p.row_ptr[r + 1];
+                for (int64_t e = e0 + lane; e < e1; e += 32)
+                    part = fmaf(p.prob[e], p.V[min((uint32_t)p.col[e], nm1)], part);
+            } else {
+                const float* row = p.P + r * p.n;
+                for (int j = lane; j < p.n; j += 32) part = fmaf(row[j], p.V[j], part);
+            }
+            for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+            const float c = p.cost[r];
+            best = fminf(best, c == kInf ? kInf : fmaf(p.gamma, part, c));
+        }
+        if (lane == 0) p.W[i] = best;
+    }
+}
+
 // dL/dcost(s, pi(s)) = lambda(s); dL/dz(s, pi(s), t) = gamma lambda(s) p_t (V(j_t) - sum_u p_u V(j_u))
 __global__ void rmb_grad_kernel(int n, int m, int k, float gamma, const int32_t* __restrict__ pi,
                                 const int32_t* __restrict__ col, const float* __restrict__ prob,
@@ -1416,6 +1467,38 @@ int rmb_validate(const rmb_mdp* mdp, void* workspace, size_t workspace_bytes, vo
     if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RMB_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return RMB_ERR_CUDA;
     return h;
+}
+
+int rmb_backup_states(const rmb_mdp* mdp, const float* V, const int32_t* states, int64_t count, const int32_t* pi,
+                      float* W_out, void* stream)
+{
+    int st = check_mdp(mdp);
+    if (st) return st;
+    if (count < 0 || (count > 0 && (!V || !states || !W_out))) return RMB_ERR_ARG;
+    if (mdp->format == RMB_DENSE && mdp->p_dtype != RMB_P_F32) return RMB_ERR_UNSUPPORTED;
+    if (count == 0) return RMB_OK;
+    DevInfo* D = nullptr;
+    if ((st = dev_info(&D))) return st;
+    BL b;
+    b.n = (int)mdp->n;
+    b.m = mdp->m;
+    b.fmt = mdp->format;
+    b.P = static_cast<const float*>(mdp->P);
+    b.row_ptr = mdp->row_ptr;
+    b.col = mdp->col;
+    b.prob = mdp->prob;
+    b.cost = mdp->cost;
+    b.gamma = (float)mdp->gamma;
+    b.V = V;
+    b.states = states;
+    b.count = count;
+    b.pi = pi;
+    b.W = W_out;
+    const int64_t warps_needed = count;
+    const int64_t blocks = std::min<int64_t>((warps_needed + 7) / 8, (int64_t)D->sms * 8);
+    rmb_backup_list_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(b);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? RMB_OK : RMB_ERR_CUDA;
 }
 
 int rmb_softmax_rows(const rmb_mdp* mdp, const float* logits, float* prob_out, void* stream)

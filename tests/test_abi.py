@@ -300,3 +300,20 @@ def test_prioritized_arguments(L):
     assert call(4, 0.05, need, V=None) == rmb.RMB_ERR_ARG          # no values
     assert call(4, 0.05, need - 1) == rmb.RMB_ERR_WORKSPACE        # workspace too small
     assert call(4, 0.05, need, ws=(1 << 20) + 8) == rmb.RMB_ERR_WORKSPACE   # not 256-byte aligned
+
+
+def test_backup_states_arguments(L):
+    """rmb_backup_states: argument checks on the host; count 0 launches nothing."""
+    d = _fake_mdp()
+    f = L.rmb_backup_states
+    f.argtypes = [ctypes.POINTER(rmb.rmb_mdp), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    assert f(ctypes.byref(d), 4096, 8192, -1, None, 4096, None) == rmb.RMB_ERR_ARG      # negative count
+    assert f(ctypes.byref(d), None, 8192, 5, None, 4096, None) == rmb.RMB_ERR_ARG      # no values
+    assert f(ctypes.byref(d), 4096, None, 5, None, 4096, None) == rmb.RMB_ERR_ARG      # no states
+    assert f(ctypes.byref(d), 4096, 8192, 5, None, None, None) == rmb.RMB_ERR_ARG      # no output
+    assert f(ctypes.byref(d), None, None, 0, None, None, None) == rmb.RMB_OK           # nothing to do
+    dd = _fake_mdp(fmt=rmb.RMB_DENSE)
+    dd.p_dtype = rmb.RMB_P_BF16
+    assert f(ctypes.byref(dd), 4096, 8192, 5, None, 4096, None) == rmb.RMB_ERR_UNSUPPORTED
