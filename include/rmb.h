@@ -148,6 +148,15 @@ typedef struct {
    same sweep have already landed (chaotic relaxation; b is ignored).  One barrier per sweep keeps
    the stop test.  Converges to the same fixed point; trajectories are not reproducible. */
 #define RMB_FLAG_ASYNC 4
+/* rmb_vi picks a one-cluster solve for small MDPs with small batches: up to 16 CTAs of one thread-block
+   cluster each hold a copy of the values (and of the order) in shared memory, exchange every batch's
+   new values through distributed shared memory and separate batches by the hardware cluster barrier
+   instead of a grid-wide barrier through memory (stats->path = 4).  It is taken when n * 16 bytes fit
+   in shared memory (n <= 14080), the sweep has >= 2 batches of at most 2 states per warp of the cluster
+   (b <= 512 with 16 CTAs of 512 threads), rows are CSR or float32 dense, the order is sigma (RMB_SELECT_PERMUTATION),
+   the stop test RMB_RESIDUAL_SWEEP, grid_ctas = 0 and neither RMB_FLAG_ASYNC nor
+   RMB_FLAG_INJECT_BARRIER_STALL is set.  This flag keeps the grid-wide solve instead. */
+#define RMB_FLAG_NO_CLUSTER 8
 
 /* Results of a solve (filled only when a stats pointer is passed). */
 typedef struct {
@@ -158,7 +167,8 @@ typedef struct {
     double v_shift;          /* centring offset mu at exit */
     int32_t status;          /* device-side rmb_status */
     int32_t grid_ctas;       /* CTAs of the persistent launch */
-    int32_t path;            /* 0 dense, 1 CSR vectorised rows, 2 CSR generic rows, 3 dense TMA pipeline */
+    int32_t path;            /* 0 dense, 1 CSR vectorised rows, 2 CSR generic rows, 3 dense TMA pipeline,
+                                4 one-cluster solve of a small MDP (RMB_FLAG_NO_CLUSTER) */
     int32_t lanes_per_state; /* CSR paths: lanes that share one state */
     float ms;                /* device time of the call (CUDA events on `stream`) */
     int32_t batch;           /* the mini-batch size b used (the model's choice when opts.batch = 0) */
@@ -356,7 +366,7 @@ int rmb_fixed_point_grad(const rmb_mdp *mdp, const int32_t *pi, const float *V, 
  * a single CTA are taken at run time from one shared queue, longest estimate first, by whichever CTA
  * is free (a group's CTAs join once their MDP is solved); the workspace's first 4 bytes hold the
  * queue cursor, which rmb_batched_run resets.  Results per MDP are identical to rmb_vi with the same
- * b, seed and options.
+ * b, seed and options and RMB_FLAG_NO_CLUSTER (the grid-wide solve, whose sums run in the same order).
  *
  * 1. rmb_batched_workspace_bytes(items, count, opts): workspace size for this plan.
  * 2. rmb_batched_plan(...): plans, writes the kernel parameters into the workspace (synchronous) and

@@ -39,9 +39,10 @@ RMB_P_FP8E4M3 = 2
 RMB_FLAG_INJECT_BARRIER_STALL = 1
 RMB_FLAG_RAW_ROWS = 2
 RMB_FLAG_ASYNC = 4
+RMB_FLAG_NO_CLUSTER = 8
 RMB_SELECT_PERMUTATION, RMB_SELECT_UNIFORM, RMB_SELECT_WEIGHTED = 0, 1, 2
 RMB_RESIDUAL_SWEEP, RMB_RESIDUAL_BELLMAN = 0, 1
-PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic", 3: "dense-tma"}
+PATH_NAMES = {0: "dense", 1: "csr-vec", 2: "csr-generic", 3: "dense-tma", 4: "cluster"}
 
 
 class rmb_mdp(ctypes.Structure):

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "librmb.so")
 # one translation unit per kernel family, compiled in parallel and linked into one library
-SOURCES = [os.path.join(CSRC, f) for f in ("rmb.cu", "rmb_csr.cu", "rmb_dense.cu")]
+SOURCES = [os.path.join(CSRC, f) for f in ("rmb.cu", "rmb_csr.cu", "rmb_dense.cu", "rmb_small.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, "rmb_core.cuh"), os.path.join(CSRC, "rmb_device.cuh"),
                   os.path.join(ROOT, "include", "rmb.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

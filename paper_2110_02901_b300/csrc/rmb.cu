@@ -890,6 +890,53 @@ int solve(const Call& q)
     // (fewer CTAs at every grid barrier, no two sharing an SM)
     if (O->grid_ctas == 0 && path == PATH_DENSE && b < grid) grid = (int)std::max<int64_t>(b, D->sms);
 
+    // Small MDPs with small batches: one thread-block cluster runs the whole MB-VI solve with the values
+    // in shared memory and cluster barriers between batches (rmb_small.cu), when the values, orders and
+    // row offsets fit (16 bytes per state), every batch fits the cluster's warps (<= 2 states each) and the solve
+    // is the paper's plain form (sigma order, sweep-change stop, float32 rows).
+    int cluster = 0;
+    if (q.mode == MODE_VI && O->grid_ctas == 0 && select == RMB_SELECT_PERMUTATION && rkind == RMB_RESIDUAL_SWEEP &&
+        !(O->flags & (RMB_FLAG_ASYNC | RMB_FLAG_INJECT_BARRIER_STALL | RMB_FLAG_NO_CLUSTER)) && p.T >= 2 &&
+        (M->format == RMB_CSR || p.p_dtype == RMB_P_F32) && !std::getenv("RMB_NO_CLUSTER")) {
+        // dense rows of <= 2048 values (n % 4 == 0, m <= 16) are staged per warp: + 8 KB per warp
+        const bool dstage = M->format == RMB_DENSE && (M->n & 3) == 0 && (((uintptr_t)M->P) & 15) == 0 && M->m <= 16 &&
+                            (int64_t)M->m * M->n <= 2048;
+        const size_t csmem = (((size_t)M->n * 16 + 4 + 15) & ~(size_t)15) + (dstage ? (size_t)(kSmallThreads / 32) * 8192 : 0);
+        const void* cfn = small_kernel_ptr();
+        if (csmem <= (size_t)kSmallMaxDyn &&
+            cudaFuncSetAttribute(cfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem) == cudaSuccess) {
+            cudaFuncSetAttribute(cfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            for (int c : {16, 8, 4, 2}) {
+                if (b > (int64_t)kSmallMaxPer * c * (kSmallThreads / 32)) break;
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)c;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3((unsigned)c);
+                cfg.blockDim = dim3(kSmallThreads);
+                cfg.dynamicSmemBytes = csmem;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int ncl = 0;
+                if (cudaOccupancyMaxActiveClusters(&ncl, cfn, &cfg) == cudaSuccess && ncl >= 1) {
+                    cluster = c;
+                    break;
+                }
+                cudaGetLastError();
+            }
+            if (cluster) {
+                fn = cfn;
+                threads = kSmallThreads;
+                smem = csmem;
+                path = PATH_CLUSTER;
+                p.path = M->format == RMB_DENSE ? PATH_DENSE : PATH_CSR_GEN;   // the row form the kernel reads
+            }
+        }
+    }
+    if (cluster) grid = cluster;
+
     cudaStream_t s = q.stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (q.stats) {
@@ -909,7 +956,24 @@ int solve(const Call& q)
         if (cudaGetLastError() != cudaSuccess) return RMB_ERR_CUDA;
     }
     void* args[] = {&p};
-    cudaError_t ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+    cudaError_t ce;
+    if (cluster) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cluster;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)cluster);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        ce = cudaLaunchKernelExC(&cfg, fn, args);
+    } else {
+        ce = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, smem, s);
+    }
     g_launches++;
     if (ce != cudaSuccess) {
         cudaGetLastError();
@@ -933,7 +997,7 @@ int solve(const Call& q)
     q.stats->status = h.status != 0 ? h.status : h.error;
     q.stats->grid_ctas = grid;
     q.stats->path = path;
-    q.stats->lanes_per_state = path == PATH_DENSE ? threads : p.lps_all;
+    q.stats->lanes_per_state = path == PATH_DENSE ? threads : (path == PATH_CLUSTER ? 32 : p.lps_all);
     q.stats->ms = ms;
     q.stats->batch = (int32_t)b;
     return q.stats->status;

@@ -40,7 +40,7 @@
 namespace rmb {
 
 enum Mode { MODE_VI = 0, MODE_EVAL = 1, MODE_MPI = 2, MODE_GREEDY = 3 };
-enum Path { PATH_DENSE = 0, PATH_CSR_VEC = 1, PATH_CSR_GEN = 2, PATH_DENSE_TMA = 3 };
+enum Path { PATH_DENSE = 0, PATH_CSR_VEC = 1, PATH_CSR_GEN = 2, PATH_DENSE_TMA = 3, PATH_CLUSTER = 4 };
 enum Kind { K_MIN = 0, K_POLICY = 1, K_GREEDY = 2 };
 
 constexpr int kCsrThreads = 512;
@@ -1656,5 +1656,9 @@ const void* csr_gen_kernel_ptr();                    // rmb_csr_gen_kernel
 const void* dense_kernel_ptr(int p_dtype);           // rmb_dense_kernel<DT>
 const void* dense_tma_kernel_ptr(int p_dtype);       // rmb_dense_tma_kernel<DT>
 const void* batched_kernel_ptr();                    // rmb_batched_kernel
+const void* small_kernel_ptr();                      // rmb_small_kernel (one cluster, values in shared memory)
+constexpr int kSmallThreads = 512;
+constexpr int kSmallMaxPer = 2;                      // states per warp and batch in rmb_small_kernel
+constexpr int kSmallMaxDyn = 220 * 1024;             // its dynamic shared memory: 16 bytes per state + 16
 
 }  // namespace rmb

@@ -57,7 +57,8 @@ def test_batched_equals_single_solves_and_oracle():
         assert res[i]["status"] == rmb.RMB_OK, (i, res[i])
         V1 = torch.zeros(m.n, dtype=torch.float32, device="cuda")
         pi1 = torch.empty(m.n, dtype=torch.int32, device="cuda")
-        st = rmb.rmb_vi(dm, rmb.Opts(batch=plan[i]["batch"], seed=12345, eps=1e-6, max_sweeps=100000), V1, pi1)
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=plan[i]["batch"], seed=12345, eps=1e-6, max_sweeps=100000,
+                                     flags=rmb.RMB_FLAG_NO_CLUSTER), V1, pi1)
         assert st["sweeps"] == res[i]["sweeps"], i
         assert torch.equal(V1, Vs[i]), i
         assert torch.equal(pi1, pis[i]), i
@@ -109,7 +110,7 @@ def test_batched_fixed_batch_sizes_are_respected():
 def test_batched_full_config_against_single_solves_and_oracle():
     """The bench's batched workload at full size (256 MDPs, n log-uniform in [256, 65536], m in 2..16,
     k = 16) in one launch with the autotuned plan: every MDP converges; every MDP's values, policy and
-    sweep count equal a single rmb_vi solve at its planned b bit for bit; and 64 MDPs, every fourth
+    sweep count equal a single grid-wide rmb_vi solve at its planned b bit for bit; and 64 MDPs, every fourth
     by size, equal the FP64 oracle's MB-VI at their planned b."""
     mdps = mdpgen.config3()
     opts = rmb.Opts(batch=1, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000)
@@ -122,7 +123,7 @@ def test_batched_full_config_against_single_solves_and_oracle():
         V1 = torch.zeros(mdps[i].n, dtype=torch.float32, device="cuda")
         pi1 = torch.empty(mdps[i].n, dtype=torch.int32, device="cuda")
         st = rmb.rmb_vi(dm, rmb.Opts(batch=plan[i]["batch"], seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000,
-                                     validate=False), V1, pi1)
+                                     validate=False, flags=rmb.RMB_FLAG_NO_CLUSTER), V1, pi1)
         assert st["sweeps"] == res[i]["sweeps"], i
         assert torch.equal(V1, Vs[i]), i
         assert torch.equal(pi1, pis[i]), i

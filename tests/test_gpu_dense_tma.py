@@ -54,7 +54,7 @@ def test_tma_vi_trajectory(storage, n, m, b):
     V0 = mdpgen.random_values(n, seed=2)
     ref = oracle.mbvi(ref_mdp, b, seed=11, eps=0.0, max_sweeps=3, V0=V0, traj=True)
     V = torch.from_numpy(V0).cuda()
-    st = rmb.rmb_vi(form, rmb.Opts(batch=b, seed=11, eps=0.0, max_sweeps=3), V)
+    st = rmb.rmb_vi(form, rmb.Opts(batch=b, seed=11, eps=0.0, max_sweeps=3, flags=rmb.RMB_FLAG_NO_CLUSTER), V)
     assert st["path"] == "dense-tma" and st["sweeps"] == 3
     close(V.cpu().numpy(), ref["traj"][2])
 
@@ -93,7 +93,8 @@ def test_tma_converged_with_policy_and_against_the_old_path(monkeypatch):
         V = torch.zeros(n, dtype=torch.float32, device="cuda")
         pi = torch.empty(n, dtype=torch.int32, device="cuda")
         gap = torch.empty(n, dtype=torch.float32, device="cuda")
-        st = rmb.rmb_vi(dm, rmb.Opts(batch=512, seed=2, eps=1e-6, max_sweeps=100000), V, pi, gap)
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=512, seed=2, eps=1e-6, max_sweeps=100000, flags=rmb.RMB_FLAG_NO_CLUSTER),
+                        V, pi, gap)
         assert st["path"] == ("dense-tma" if tma else "dense")
         close(V.cpu().numpy(), ref["V"])
         out[tma] = (pi.cpu().numpy(), gap.cpu().numpy())

@@ -31,11 +31,12 @@ def test_maze_trajectory_matches_oracle(b):
     mdp = mdpgen.maze(40, 1500, gamma=0.95, slip=0.2, seed=9)
     ref = oracle.mbvi(mdp, b, seed=31, eps=0.0, max_sweeps=12, traj=True)
     dm = rmb.DeviceMDP.from_host(mdp)
-    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
-    st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=31, eps=0.0, max_sweeps=12), V)
-    assert st["path"] == "csr-generic" and st["sweeps"] == 12
     want = ref["traj"][-1]
-    assert np.max(np.abs(V.cpu().numpy() - want)) <= 1e-5 * max(1.0, np.abs(want).max())
+    for flags, path in ((rmb.RMB_FLAG_NO_CLUSTER, "csr-generic"), (0, "cluster" if b <= 512 else "csr-generic")):
+        V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=31, eps=0.0, max_sweeps=12, flags=flags), V)
+        assert st["path"] == path and st["sweeps"] == 12
+        assert np.max(np.abs(V.cpu().numpy() - want)) <= 1e-5 * max(1.0, np.abs(want).max())
 
 
 def test_maze80_sweeps_to_accuracy_match_oracle():

@@ -39,13 +39,13 @@ def to_np(t):
     return t.detach().cpu().numpy()
 
 
-def gpu_vi(dm, b, seed, eps, max_sweeps, V0=None, start_sweep=0, validate=True, want_policy=True):
+def gpu_vi(dm, b, seed, eps, max_sweeps, V0=None, start_sweep=0, validate=True, want_policy=True, flags=0):
     V = torch.zeros(dm.n, dtype=torch.float32, device="cuda") if V0 is None else \
         torch.from_numpy(np.asarray(V0, np.float32)).cuda()
     pi = torch.empty(dm.n, dtype=torch.int32, device="cuda") if want_policy else None
     gap = torch.empty(dm.n, dtype=torch.float32, device="cuda") if want_policy else None
     st = rmb.rmb_vi(dm, rmb.Opts(batch=b, seed=seed, eps=eps, max_sweeps=max_sweeps, start_sweep=start_sweep,
-                                 validate=validate), V, pi, gap)
+                                 validate=validate, flags=flags), V, pi, gap)
     return to_np(V), (to_np(pi) if pi is not None else None), (to_np(gap) if gap is not None else None), st
 
 
@@ -130,13 +130,15 @@ def test_csr_generic_rows_ragged_and_inadmissible():
     V0 = mdpgen.random_values(mdp.n, seed=1)
     for b in (1, 50, 1500):
         ref = oracle.mbvi(mdp, b, seed=3, eps=0.0, max_sweeps=4, V0=V0, traj=True)
-        V, _, _, st = gpu_vi(dm, b, 3, 0.0, 4, V0=V0, want_policy=False)
-        assert st["path"] == "csr-generic"
-        close(V, ref["traj"][3])
+        for flags, path in ((rmb.RMB_FLAG_NO_CLUSTER, "csr-generic"), (0, "cluster" if b <= 512 else "csr-generic")):
+            V, _, _, st = gpu_vi(dm, b, 3, 0.0, 4, V0=V0, want_policy=False, flags=flags)
+            assert st["path"] == path
+            close(V, ref["traj"][3])
     ref = oracle.mbvi(mdp, 50, seed=3, eps=1e-6, max_sweeps=5000)
-    V, pi, gap, st = gpu_vi(dm, 50, 3, 1e-6, 5000)
-    close(V, ref["V"])
-    assert np.all(np.isfinite(mdp.cost[np.arange(mdp.n) * mdp.m + pi]))
+    for flags in (rmb.RMB_FLAG_NO_CLUSTER, 0):
+        V, pi, gap, st = gpu_vi(dm, 50, 3, 1e-6, 5000, flags=flags)
+        close(V, ref["V"])
+        assert np.all(np.isfinite(mdp.cost[np.arange(mdp.n) * mdp.m + pi]))
 
 
 @pytest.mark.parametrize("k", [12, 30])
@@ -144,9 +146,10 @@ def test_csr_generic_path_for_uniform_rows_not_vectorisable(k):
     mdp = mdpgen.csr_uniform_k(900, 3, k, gamma=0.9, seed=k)
     dm = rmb.DeviceMDP.from_host(mdp)
     ref = oracle.mbvi(mdp, 40, seed=1, eps=0.0, max_sweeps=3, traj=True)
-    V, _, _, st = gpu_vi(dm, 40, 1, 0.0, 3, want_policy=False)
-    assert st["path"] == "csr-generic"
-    close(V, ref["traj"][2])
+    for flags, path in ((rmb.RMB_FLAG_NO_CLUSTER, "csr-generic"), (0, "cluster")):
+        V, _, _, st = gpu_vi(dm, 40, 1, 0.0, 3, want_policy=False, flags=flags)
+        assert st["path"] == path
+        close(V, ref["traj"][2])
 
 
 # ------------------------------------------------------------------------------------------------
@@ -154,19 +157,24 @@ def test_dense_config1_full_size():
     mdp = mdpgen.config1()
     dm = rmb.DeviceMDP.from_host(mdp)
     ref = oracle.mbvi(mdp, 50, seed=mdpgen.PERM_SEED, eps=0.0, max_sweeps=5, traj=True)
-    for s in (1, 5):
-        V, _, _, st = gpu_vi(dm, 50, mdpgen.PERM_SEED, 0.0, s, want_policy=False)
-        assert st["path"] == "dense"
-        close(V, ref["traj"][s - 1])
+    # both solvers: the one-cluster solve this workload takes by default, and the grid-wide one
+    for flags, path in ((0, "cluster"), (rmb.RMB_FLAG_NO_CLUSTER, "dense")):
+        for s in (1, 5):
+            V, _, _, st = gpu_vi(dm, 50, mdpgen.PERM_SEED, 0.0, s, want_policy=False, flags=flags)
+            assert st["path"] == path
+            close(V, ref["traj"][s - 1])
     ref = oracle.mbvi(mdp, 50, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=100000)
-    V, pi, gap, st = gpu_vi(dm, 50, mdpgen.PERM_SEED, 1e-6, 100000)
-    assert st["status"] == rmb.RMB_OK and abs(st["sweeps"] - ref["sweeps"]) <= max(2, 0.02 * ref["sweeps"])
-    close(V, ref["V"])
     jstar, pistar, _ = exact.policy_iteration(mdp)
-    close(V, jstar)
     _, _, jgap, _ = exact.bellman_pass(mdp, jstar)
     sel = jgap > 1e-6 * max(1.0, float(np.abs(jstar).max()))
-    assert np.array_equal(pi[sel], pistar[sel])
+    for flags in (0, rmb.RMB_FLAG_NO_CLUSTER):
+        V, pi, gap, st = gpu_vi(dm, 50, mdpgen.PERM_SEED, 1e-6, 100000, flags=flags)
+        assert st["status"] == rmb.RMB_OK and abs(st["sweeps"] - ref["sweeps"]) <= 2
+        if st["sweeps"] != ref["sweeps"]:   # compare at the oracle's stopping sweep
+            V, pi, gap, st = gpu_vi(dm, 50, mdpgen.PERM_SEED, 0.0, ref["sweeps"], flags=flags)
+        close(V, ref["V"])
+        close(V, jstar)
+        assert np.array_equal(pi[sel], pistar[sel])
 
 
 @pytest.mark.parametrize("n,m,stage", [(333, 3, None), (1000, 12, None), (1000, 4, "128"), (999, 2, "100")])
@@ -179,8 +187,10 @@ def test_dense_paths(n, m, stage, monkeypatch):
     V0 = mdpgen.random_values(n, seed=2)
     for b in (1, 37, n):
         ref = oracle.mbvi(mdp, b, seed=8, eps=0.0, max_sweeps=3, V0=V0, traj=True)
-        V, _, _, st = gpu_vi(dm, b, 8, 0.0, 3, V0=V0, want_policy=False)
-        close(V, ref["traj"][2])
+        for flags in (rmb.RMB_FLAG_NO_CLUSTER, 0):
+            V, _, _, st = gpu_vi(dm, b, 8, 0.0, 3, V0=V0, want_policy=False, flags=flags)
+            assert st["path"] != "cluster" if flags else st["path"] == ("cluster" if b < n else "dense")
+            close(V, ref["traj"][2])
 
 
 # ------------------------------------------------------------------------------------------------
