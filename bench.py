@@ -476,10 +476,13 @@ def configs_summary(args, rmb, torch, stream, hbm, peak_kind):
     ach = (st["sweeps"] + 1) * mdp.n * mdp.m * mdp.n * 4 / (st["ms"] / 1e3) / 1e9
     e = {"workload": "dense n=500 m=4 dirichlet(1) c~U[0,1] gamma=0.95, MB-VI b=50 from V=0 to 1e-6",
          "time_to_eps_ms": ms, "sweeps": st["sweeps"], "backups_per_s": mdp.n * st["sweeps"] / (ms / 1e3),
-         "barriers": st["barriers"], "us_per_barrier": 1e3 * st["ms"] / max(1, st["barriers"]),
+         "barriers": st["barriers"], "us_per_barrier": 1e3 * st["ms"] / max(1, st["barriers"]), "path": st["path"],
          "roofline": {"bound": "latency", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                      "peak_kind": peak_kind, "note": "P (4 MB) stays in L2; each of the 10 batches per sweep "
-                                                      "costs one grid barrier and a chain of L2 round trips"}}
+                      "peak_kind": peak_kind,
+                      "kernel": "rmb_small_kernel" if st["path"] == "cluster" else "rmb_dense_kernel<f32>",
+                      "note": "P (4 MB) stays in L2; each of the 10 batches per sweep costs one barrier (a "
+                              "hardware cluster barrier on the one-cluster path) plus the exchange of the "
+                              "batch's values"}}
     if not args.no_cpu:
         import oracle
         t0 = time.perf_counter()
@@ -686,6 +689,7 @@ def _dense500(args, world, rmb, torch, stream, hbm, peak_kind):
         step()
     ms, outs = _timed(step, args.steps, stream)
     sw = outs[-1]["sweeps"]
+    path = outs[-1]["path"]
     err, cpu = None, None
     if not args.no_cpu:   # CPU-baseline leg: the FP64 oracle's full solve, timed, and the GPU error against it
         import oracle
@@ -699,10 +703,11 @@ def _dense500(args, world, rmb, torch, stream, hbm, peak_kind):
     ach = bytes_launch / (outs[-1]["ms"] / 1e3) / 1e9
     return _line(METRIC, mdp.n * sw / (ms / 1e3), "Bellman backups/s", ms, args, world,
                  {"workload": "dense-mdp n=500 m=4 dirichlet(1) c~U[0,1] gamma=0.95; MB-VI b=50 from V=0 to 1e-6",
-                  "sweeps": sw, "barriers_per_solve": outs[-1]["barriers"], "time_to_eps_ms": ms,
+                  "sweeps": sw, "barriers_per_solve": outs[-1]["barriers"], "time_to_eps_ms": ms, "path": path,
                   "max_abs_err_vs_oracle": err, "l2": "P is 4 MB: L2-resident by design (latency-bound workload)"},
                  roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                           "traffic": None, "kernel": "rmb_dense_kernel<f32>", "peak_kind": peak_kind,
+                           "traffic": None, "peak_kind": peak_kind,
+                           "kernel": "rmb_small_kernel" if path == "cluster" else "rmb_dense_kernel<f32>",
                            "note": "P is L2-resident; the bound is the per-batch barrier latency (10 batches/sweep)"},
                  cpu_baseline=cpu)
 
@@ -1059,7 +1064,7 @@ def _maze(args, world, rmb, torch, stream, hbm, peak_kind):
                   "table": rows, "reference_solutions": lines, "paper_speedups_gtx1650ti": PAPER_MAZE,
                   "l2": "P is < 3 MB: L2-resident (latency-bound workload)"},
                  roofline={"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                           "traffic": None, "kernel": "rmb_csr_gen_kernel", "peak_kind": peak_kind,
+                           "traffic": None, "kernel": "rmb_small_kernel (b <= 512) / rmb_csr_gen_kernel", "peak_kind": peak_kind,
                            "note": "latency-bound: P (2.6 MB) is L2-resident; a batch costs a barrier plus a "
                                    "few dependent L2 round trips, so HBM is not the bound"},
                  cpu_baseline=cpu)
