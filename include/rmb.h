@@ -153,7 +153,8 @@ typedef struct {
    new values through distributed shared memory and separate batches by the hardware cluster barrier
    instead of a grid-wide barrier through memory (stats->path = 4).  It is taken when n * 16 bytes fit
    in shared memory (n <= 14080), the sweep has >= 2 batches of at most 2 states per warp of the cluster
-   (b <= 512 with 16 CTAs of 512 threads), rows are CSR or float32 dense, the order is sigma (RMB_SELECT_PERMUTATION),
+   (b <= 512 with 16 CTAs of 512 threads), rows are float32 dense or CSR (vectorisable uniform rows of
+   <= 256 entries per state, other uniform rows of <= 32, or ragged rows), the order is sigma (RMB_SELECT_PERMUTATION),
    the stop test RMB_RESIDUAL_SWEEP, grid_ctas = 0 and neither RMB_FLAG_ASYNC nor
    RMB_FLAG_INJECT_BARRIER_STALL is set.  This flag keeps the grid-wide solve instead. */
 #define RMB_FLAG_NO_CLUSTER 8

@@ -902,8 +902,21 @@ int solve(const Call& q)
         const bool dstage = M->format == RMB_DENSE && (M->n & 3) == 0 && (((uintptr_t)M->P) & 15) == 0 && M->m <= 16 &&
                             (int64_t)M->m * M->n <= 2048;
         const size_t csmem = (((size_t)M->n * 16 + 4 + 15) & ~(size_t)15) + (dstage ? (size_t)(kSmallThreads / 32) * 8192 : 0);
-        const void* cfn = small_kernel_ptr();
-        if (csmem <= (size_t)kSmallMaxDyn &&
+        // vectorisable CSR rows are read as float4 / int4 chunks, <= 2 per lane of the state's warp;
+        // larger uniform rows stay on the grid (the cluster would read them row by row)
+        int cnc = 0;
+        bool rows_ok = true;
+        if (path == PATH_CSR_VEC) {
+            const int64_t chunks = (int64_t)M->m * (M->k_uniform >> 2);
+            const int k4 = M->k_uniform >> 2;
+            cnc = chunks <= 32 ? 1 : (chunks <= 64 ? 2 : 0);
+            rows_ok = cnc > 0 && k4 <= 32;
+            if (!rows_ok) cnc = 0;
+        } else if (M->format == RMB_CSR && M->k_uniform > 0) {
+            rows_ok = (int64_t)M->m * M->k_uniform <= 32;   // uniform but not vectorisable: one entry per lane
+        }
+        const void* cfn = small_kernel_ptr(cnc);
+        if (rows_ok && csmem <= (size_t)kSmallMaxDyn &&
             cudaFuncSetAttribute(cfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem) == cudaSuccess) {
             cudaFuncSetAttribute(cfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             for (int c : {16, 8, 4, 2}) {
@@ -931,7 +944,8 @@ int solve(const Call& q)
                 threads = kSmallThreads;
                 smem = csmem;
                 path = PATH_CLUSTER;
-                p.path = M->format == RMB_DENSE ? PATH_DENSE : PATH_CSR_GEN;   // the row form the kernel reads
+                // the row form the kernel reads: dense, vectorised CSR (cnc > 0) or one entry per lane
+                p.path = M->format == RMB_DENSE ? PATH_DENSE : (cnc > 0 ? PATH_CSR_VEC : PATH_CSR_GEN);
             }
         }
     }
@@ -1287,9 +1301,14 @@ int batched_ctas(int* ctas)
     DevInfo* D = nullptr;
     int st = dev_info(&D);
     if (st) return st;
-    cudaFuncSetAttribute(batched_kernel_ptr(), cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    // single-CTA MDPs of up to kSoloMaxN states keep their values in kSoloMaxN * 4 bytes of dynamic
+    // shared memory (SoloRun); the rest of the unified L1 stays cache
+    if (cudaFuncSetAttribute(batched_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, kSoloMaxN * 4) !=
+        cudaSuccess)
+        return RMB_ERR_CUDA;
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel_ptr(), kCsrThreads, 0) != cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel_ptr(), kCsrThreads, kSoloMaxN * 4) !=
+            cudaSuccess || occ < 1)
         return RMB_ERR_CUDA;
     *ctas = D->sms;   // one CTA per SM (the kernel is register-bound to one 512-thread CTA per SM)
     return RMB_OK;
@@ -1386,8 +1405,8 @@ int rmb_batched_run(const rmb_batch_handle* h, void* stream)
     int nqueue = h->nqueue;
     int* qnext = reinterpret_cast<int*>(ws);
     void* args[] = {(void*)&kps, (void*)&toff, (void*)&tasks, (void*)&nqueue, (void*)&qnext};
-    const cudaError_t ce = cudaLaunchCooperativeKernel(batched_kernel_ptr(),
-                                                       dim3(h->grid_ctas), dim3(kCsrThreads), args, 0, s);
+    const cudaError_t ce = cudaLaunchCooperativeKernel(batched_kernel_ptr(), dim3(h->grid_ctas), dim3(kCsrThreads),
+                                                       args, (size_t)kSoloMaxN * 4, s);
     g_launches++;
     if (ce != cudaSuccess) {
         cudaGetLastError();

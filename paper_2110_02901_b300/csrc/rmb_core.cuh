@@ -528,9 +528,25 @@ __device__ __forceinline__ void fast_load(const KP& p, int s, bool act, int lps,
     }
 }
 
+__device__ __forceinline__ float lds_f32(uint32_t saddr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(saddr));
+    return v;
+}
+
+// a successor value from the values A: global memory (L1-cached, see gather), or, with SM, A is in
+// this CTA's shared memory
+template <bool SM>
+__device__ __forceinline__ float gather_v(const float* __restrict__ A, int j, uint32_t nm1)
+{
+    if (SM) return lds_f32((uint32_t)__cvta_generic_to_shared(A) + 4u * min((uint32_t)j, nm1));
+    return gather(A, j, nm1);
+}
+
 // min (and, with ARG, the lowest arg-min and the second smallest value) over the state's rows of
 // c + gamma * sum p * A[col]; every lane of the group gets the result
-template <bool ARG, int NC>
+template <bool ARG, int NC, bool SM = false>
 __device__ __forceinline__ Best fast_eval(const KP& p, const StateRegs<NC>& R, const float* __restrict__ A, int lps,
                                           int lane_g)
 {
@@ -538,8 +554,8 @@ __device__ __forceinline__ Best fast_eval(const KP& p, const StateRegs<NC>& R, c
     float part[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const float g0 = gather(A, R.c[c].x, nm1), g1 = gather(A, R.c[c].y, nm1);
-        const float g2 = gather(A, R.c[c].z, nm1), g3 = gather(A, R.c[c].w, nm1);
+        const float g0 = gather_v<SM>(A, R.c[c].x, nm1), g1 = gather_v<SM>(A, R.c[c].y, nm1);
+        const float g2 = gather_v<SM>(A, R.c[c].z, nm1), g3 = gather_v<SM>(A, R.c[c].w, nm1);
         part[c] = fmaf(R.p[c].x, g0, fmaf(R.p[c].y, g1, fmaf(R.p[c].z, g2, R.p[c].w * g3)));
     }
     const int k4 = 1 << p.k4_log2;
@@ -1639,6 +1655,221 @@ struct Runner {
 };
 
 // ------------------------------------------------------------------------------------------------
+// MB-VI of one CSR MDP (vectorised rows) on one CTA with the values in its shared memory (a queue task
+// of the batched launch).  The same state arithmetic as Runner (fast_load / fast_eval, the same lanes
+// per state, centred values, the same re-centring), so results equal rmb_vi's grid solve bit for bit;
+// successor values come from shared memory instead of L2.  One buffer suffices: a batch's states read
+// the values from before the batch, their (state, value) pairs go to the workspace lists S / W, and a
+// CTA barrier later they are written into the values.
+// ------------------------------------------------------------------------------------------------
+template <int NCA>
+struct SoloRun {
+    const KP& p;
+    RedSmem& rs;
+    float* Vs;          // n centred values (shared memory)
+    Centre C;
+    long long syncs = 0;
+    bool perm_ok = true;
+
+    __device__ SoloRun(const KP& kp, RedSmem& r, float* v) : p(kp), rs(r), Vs(v) {}
+
+    __device__ PermKey key_for(long long k) const
+    {
+        PermKey K;
+        K.n = (uint32_t)p.n;
+        K.h = p.h;
+        K.mask = (1u << p.h) - 1u;
+        K.k0 = p.seed_lo;
+        K.k1 = p.seed_hi;
+        K.s_lo = (uint32_t)(unsigned long long)k;
+        K.s_hi = (uint32_t)((unsigned long long)k >> 32);
+        K.buf = nullptr;
+        K.select = 0;
+        K.wtot = 0;
+        K.cdf = nullptr;
+        return K;
+    }
+
+    __device__ void bar()
+    {
+        ++syncs;
+        __syncthreads();
+    }
+
+    // block-wide max |change|, min, max of the accumulators (every thread gets them)
+    __device__ void reduce(Acc& a)
+    {
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int off = 16; off > 0; off >>= 1) {
+            a.dmax = fmaxf(a.dmax, __shfl_xor_sync(0xffffffffu, a.dmax, off));
+            a.vlo = fminf(a.vlo, __shfl_xor_sync(0xffffffffu, a.vlo, off));
+            a.vhi = fmaxf(a.vhi, __shfl_xor_sync(0xffffffffu, a.vhi, off));
+        }
+        __syncthreads();
+        if (lane == 0) {
+            rs.v[0][wid] = a.dmax;
+            rs.v[1][wid] = a.vlo;
+            rs.v[2][wid] = a.vhi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < nw; ++w) {
+                a.dmax = fmaxf(a.dmax, rs.v[0][w]);
+                a.vlo = fminf(a.vlo, rs.v[1][w]);
+                a.vhi = fmaxf(a.vhi, rs.v[2][w]);
+            }
+            rs.bc[0] = a.dmax;
+            rs.bc[1] = a.vlo;
+            rs.bc[2] = a.vhi;
+        }
+        __syncthreads();
+        a.dmax = rs.bc[0];
+        a.vlo = rs.bc[1];
+        a.vhi = rs.bc[2];
+        __syncthreads();
+    }
+
+    // positions [pos0, pos0 + len) of the order K (K null: natural order): KIND K_MIN writes (state,
+    // value) into S / W[i]; K_GREEDY writes the outputs.  Rows load one step ahead (as csr_batch_fast).
+    template <int KIND>
+    __device__ void batch(int pos0, int len, const PermKey* K, Acc& acc)
+    {
+        constexpr bool ARG = (KIND == K_GREEDY);
+        const GroupView gv{0, 1};
+        const int lps = p.lps_all;
+        const FastGeom G(lps, gv);
+        if (G.first >= len) return;
+        int block_states = G.resolve(0, pos0, len, K, &perm_ok);
+        int s_cur = __shfl_sync(0xffffffffu, block_states, G.g);
+        StateRegs<NCA> cur, nxt;
+        fast_load<K_MIN, NCA>(p, s_cur < 0 ? 0 : s_cur, s_cur >= 0, lps, G.lane_g, cur);
+        for (int j = 0; G.first + j * G.U < len; ++j) {
+            const int jn = j + 1;
+            int s_nxt = -1;
+            if (G.first + jn * G.U < len) {
+                if (jn % G.per_block == 0) block_states = G.resolve(jn, pos0, len, K, &perm_ok);
+                s_nxt = __shfl_sync(0xffffffffu, block_states, (jn % G.per_block) * G.spw + G.g);
+            }
+            fast_load<K_MIN, NCA>(p, s_nxt < 0 ? 0 : s_nxt, s_nxt >= 0, lps, G.lane_g, nxt);
+            const bool lead = s_cur >= 0 && G.lane_g == 0;
+            const Best r = fast_eval<ARG, NCA, true>(p, cur, Vs, lps, G.lane_g);
+            if (lead) {
+                const float old = Vs[s_cur];
+                const float v = new_value(r.q, C);
+                if (v != v) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
+                acc.dmax = fmaxf(acc.dmax, fabsf(v - old));
+                if (KIND == K_GREEDY) {
+                    if (p.pi) st_l2(p.pi + s_cur, r.a);
+                    if (p.qgap) p.qgap[s_cur] = r.q2 - r.q;
+                    p.Vout[s_cur] = (float)(C.mu + (double)old);
+                } else {
+                    acc.vlo = fminf(acc.vlo, v);
+                    acc.vhi = fmaxf(acc.vhi, v);
+                    const int i = G.first + G.g + j * G.U;
+                    st_l2(p.S[0] + i, s_cur);
+                    st_l2(p.W[0] + i, v);
+                }
+            }
+            cur = nxt;
+            s_cur = s_nxt;
+        }
+    }
+
+    __device__ float shift_for(float lo, float hi) const
+    {
+        const float mid = 0.5f * (lo + hi);
+        const float spread = hi - lo;
+        const float floor_ = 1e-6f * (float)(fabs(C.mu) + 1.0);
+        if (!(fabsf(mid) > fmaxf(0.25f * spread, floor_))) return 0.f;
+        return mid;
+    }
+
+    __device__ void run()
+    {
+        Ctrl* c = p.ctrl;
+        if (ld_volatile(&c->error) != 0) return;
+        Acc a0 = {0.f, kInf, -kInf};
+        for (int i = threadIdx.x; i < p.n; i += blockDim.x) {
+            const float v = p.Vin[i];
+            a0.vlo = fminf(a0.vlo, v);
+            a0.vhi = fmaxf(a0.vhi, v);
+            if (v != v || fabsf(v) == kInf) atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
+        }
+        reduce(a0);
+        const double mu0 = (double)(float)(0.5 * ((double)a0.vlo + (double)a0.vhi));
+        C = make_centre(mu0, p.gamma_d);
+        for (int i = threadIdx.x; i < p.n; i += blockDim.x) Vs[i] = (float)((double)p.Vin[i] - mu0);
+        bar();
+        long long sweeps = 0;
+        double residual = 0.0;
+        bool converged = false, ok = ld_volatile(&c->error) == 0;
+        const bool ordered = p.T > 1;
+        for (long long j = 0; ok && j < p.max_sweeps; ++j) {
+            const long long k = p.start_sweep + j;
+            PermKey K = key_for(k);
+            if (p.perm_buf) {   // the whole order of the sweep, then the batches read it
+                for (int i = threadIdx.x; i < p.n; i += blockDim.x)
+                    st_l2(p.perm_buf + i, order_at((uint32_t)i, K, &perm_ok));
+                bar();
+                K.buf = p.perm_buf;
+            }
+            Acc acc = {0.f, kInf, -kInf};
+            for (int t = 0; t < p.T; ++t) {
+                const int len = (t == p.T - 1) ? p.last_len : p.b;
+                batch<K_MIN>(t * p.b, len, ordered ? &K : nullptr, acc);
+                bar();
+                for (int i = threadIdx.x; i < len; i += blockDim.x) Vs[ld_l2(p.S[0] + i)] = ld_l2(p.W[0] + i);
+                bar();
+            }
+            reduce(acc);
+            ++sweeps;
+            residual = (double)acc.dmax;
+            if (threadIdx.x == 0 && p.trace) p.trace[j] = residual;
+            if (acc.dmax != acc.dmax) {
+                atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
+                ok = false;
+                break;
+            }
+            if (ld_volatile(&c->error) != 0) {
+                ok = false;
+                break;
+            }
+            if ((double)acc.dmax <= p.eps) {
+                converged = true;
+                break;
+            }
+            // the grid solve ends its last sweep without re-centring; so does this one (same outputs)
+            const float sh = j + 1 < p.max_sweeps ? shift_for(acc.vlo, acc.vhi) : 0.f;
+            if (sh != 0.f) {
+                for (int i = threadIdx.x; i < p.n; i += blockDim.x) Vs[i] -= sh;
+                C = make_centre(C.mu + (double)sh, p.gamma_d);
+                bar();
+            }
+        }
+        if (ok) {
+            if (p.pi || p.qgap) {
+                Acc g = {0.f, kInf, -kInf};
+                batch<K_GREEDY>(0, p.n, nullptr, g);
+            } else {
+                for (int i = threadIdx.x; i < p.n; i += blockDim.x) p.Vout[i] = (float)(C.mu + (double)Vs[i]);
+            }
+        }
+        if (!perm_ok) atomicCAS(&c->error, 0, RMB_ERR_UNSUPPORTED);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            c->sweeps = sweeps;
+            c->iters = 0;
+            c->barriers = syncs;
+            c->residual = residual;
+            c->mu = C.mu;
+            int st = ld_volatile(&c->error);
+            if (st == 0 && ok && !converged) st = RMB_ERR_NOT_CONVERGED;
+            c->status = st;
+        }
+    }
+};
+
+// ------------------------------------------------------------------------------------------------
 // Batched solves: many independent MDPs in one persistent launch.  Every CTA runs a list of tasks; a
 // task is one MDP solved by a group of CTAs (its own barrier counter and control block) or by this
 // CTA alone (barriers are then CTA barriers).  CTAs of a multi-CTA group run the same task list.
@@ -1656,9 +1887,11 @@ const void* csr_gen_kernel_ptr();                    // rmb_csr_gen_kernel
 const void* dense_kernel_ptr(int p_dtype);           // rmb_dense_kernel<DT>
 const void* dense_tma_kernel_ptr(int p_dtype);       // rmb_dense_tma_kernel<DT>
 const void* batched_kernel_ptr();                    // rmb_batched_kernel
-const void* small_kernel_ptr();                      // rmb_small_kernel (one cluster, values in shared memory)
+const void* small_kernel_ptr(int nc);                // rmb_small_kernel<NC> (one cluster, values in shared memory)
 constexpr int kSmallThreads = 512;
 constexpr int kSmallMaxPer = 2;                      // states per warp and batch in rmb_small_kernel
 constexpr int kSmallMaxDyn = 220 * 1024;             // its dynamic shared memory: 16 bytes per state + 16
+constexpr int kSoloMaxN = 40960;                     // batched queue tasks up to this n keep their values in
+                                                     // shared memory (SoloRun): 160 KB of the batched launch
 
 }  // namespace rmb

@@ -42,6 +42,7 @@ rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off,
     __shared__ RedSmem rs;
     __shared__ KP s_kp;
     __shared__ int s_next;
+    extern __shared__ __align__(16) float solo_values[];   // kSoloMaxN floats: SoloRun's values
     // this CTA's own tasks (its share of the multi-CTA groups) first, then single-CTA MDPs from the
     // shared queue (longest first, after the last static task) until it is empty
     const int t0 = task_off[blockIdx.x], t1 = task_off[blockIdx.x + 1];
@@ -61,7 +62,16 @@ rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off,
         if (threadIdx.x == 0) s_kp = kps[bt.item];
         __syncthreads();
         const GroupView gv{bt.rank, bt.size};
-        if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 1 && s_kp.nc_one == 1) {
+        // an MDP solved by this CTA alone keeps its values in shared memory when they fit
+        const bool solo = bt.size == 1 && s_kp.path == PATH_CSR_VEC && s_kp.n <= kSoloMaxN && s_kp.select == 0 &&
+                          s_kp.residual_kind == 0 && (s_kp.flags & RMB_FLAG_ASYNC) == 0;
+        if (solo && s_kp.nc_all == 1) {
+            SoloRun<1> R(s_kp, rs, solo_values);
+            R.run();
+        } else if (solo && s_kp.nc_all == 2) {
+            SoloRun<2> R(s_kp, rs, solo_values);
+            R.run();
+        } else if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 1 && s_kp.nc_one == 1) {
             Runner<PATH_CSR_VEC, 1, 1> R(s_kp, rs, nullptr, nullptr, gv);
             R.run();
         } else if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 2 && s_kp.nc_one == 1) {

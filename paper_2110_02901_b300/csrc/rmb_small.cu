@@ -43,6 +43,13 @@ struct Ahead {
     float c, pr;
     int col;
 };
+template <int NC>
+struct AheadVec {
+    StateRegs<NC> R;
+};
+template <>
+struct AheadVec<0> {
+};
 
 constexpr int kListSlots = kSmallWarps * kSmallMaxPer;   // (state, value) pairs one CTA writes per batch
 
@@ -103,6 +110,9 @@ __device__ __forceinline__ void cl_hw_barrier()
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
+// NC > 0: CSR rows of uniform length k (k % 4 == 0) read as float4 / int4 chunks, NC per lane with all 32
+// lanes of a warp on one state (fast_load / fast_eval of the grid path, gathers from shared memory)
+template <int NC>
 struct SmallRun {
     const KP& p;
     SmallSmem& sm;
@@ -280,12 +290,17 @@ struct SmallRun {
     __device__ float* warp_stage() const { return stage + (size_t)(threadIdx.x >> 5) * (kDenseAhead * 128); }
 
     // rows of state s ahead of its batch (s < 0: none); with_stage: this slot may use the staging area
-    __device__ void load(int s, Ahead& h, bool with_stage) const
+    __device__ void load(int s, Ahead& h, AheadVec<NC>& hv, bool with_stage) const
     {
         const int lane = threadIdx.x & 31;
         h.s = s;
         h.fast = false;
         if (s < 0) return;
+        if constexpr (NC > 0) {
+            h.fast = true;
+            fast_load<K_MIN, NC>(p, s, true, 32, lane, hv.R);
+            return;
+        }
         if (p.path == PATH_DENSE) {
             if (!with_stage || !stage) return;
             h.fast = true;
@@ -320,9 +335,10 @@ struct SmallRun {
 
     // Q-factors of a state whose rows were loaded ahead (falls back to eval() otherwise)
     template <bool ARG>
-    __device__ Best compute(const Ahead& h, const float* A) const
+    __device__ Best compute(const Ahead& h, const AheadVec<NC>& hv, const float* A) const
     {
         const int lane = threadIdx.x & 31;
+        if constexpr (NC > 0) return fast_eval<ARG, NC, true>(p, hv.R, A, 32, lane);
         if (!h.fast) return eval<ARG>(h.s, A);
         Best cur = {kInf, 0x7fffffff, kInf};
         if (p.path == PATH_DENSE) {
@@ -501,12 +517,13 @@ struct SmallRun {
         // rows of this warp's states of the next batch, loaded between the arrival at and the wait on
         // the barrier before it (dense: the first slot uses the warp's staging area)
         Ahead ah[kSmallMaxPer];
+        AheadVec<NC> av[kSmallMaxPer];
         auto prefetch = [&](const int32_t* order, int t) {
             const int len = batch_len(t);
 #pragma unroll
             for (int r = 0; r < kSmallMaxPer; ++r) {
                 const int i = my_pos(r);
-                load(i < len ? order[t * p.b + i] : -1, ah[r], r == 0);
+                load(i < len ? order[t * p.b + i] : -1, ah[r], av[r], r == 0);
             }
         };
         if (ok) prefetch(pbuf(p.start_sweep), 0);
@@ -525,7 +542,7 @@ struct SmallRun {
                     int2 e = make_int2(-1, 0);
                     if (ah[r].s >= 0) {
                         const int s = ah[r].s;
-                        const Best q = compute<false>(ah[r], V);
+                        const Best q = compute<false>(ah[r], av[r], V);
                         const float v = new_value(q.q, Ce);
                         if (lane == 0) {
                             if (v != v) raise(RMB_ERR_NONFINITE);
@@ -576,7 +593,10 @@ struct SmallRun {
             for (uint32_t i = lo + threadIdx.x; i < hi; i += kSmallThreads) p.Vout[i] = (float)(Ce.mu + (double)V[i]);
             if (p.pi || p.qgap) {
                 for (uint32_t i = lo + (threadIdx.x >> 5); i < hi; i += kSmallWarps) {
-                    const Best q = eval<true>((int)i, V);
+                    Ahead h;
+                    AheadVec<NC> hv;
+                    if constexpr (NC > 0) load((int)i, h, hv, false);
+                    const Best q = NC > 0 ? compute<true>(h, hv, V) : eval<true>((int)i, V);
                     if (lane == 0) {
                         if (p.pi) p.pi[i] = q.a;
                         if (p.qgap) p.qgap[i] = q.q2 - q.q;
@@ -602,6 +622,7 @@ struct SmallRun {
     }
 };
 
+template <int NC>
 __global__ void __launch_bounds__(kSmallThreads, 1) rmb_small_kernel(KP p)
 {
     __shared__ SmallSmem sm;
@@ -617,10 +638,15 @@ __global__ void __launch_bounds__(kSmallThreads, 1) rmb_small_kernel(KP p)
     float* st = dense_stage ? reinterpret_cast<float*>(dyn + (((size_t)p.n * 16 + 4 + 15) & ~(size_t)15)) : nullptr;
     uint32_t C;
     asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(C));
-    SmallRun R(p, sm, v, p0, p1, ro, st, C);
+    SmallRun<NC> R(p, sm, v, p0, p1, ro, st, C);
     R.run();
 }
 
-const void* small_kernel_ptr() { return reinterpret_cast<const void*>(rmb_small_kernel); }
+const void* small_kernel_ptr(int nc)
+{
+    if (nc == 1) return reinterpret_cast<const void*>(rmb_small_kernel<1>);
+    if (nc == 2) return reinterpret_cast<const void*>(rmb_small_kernel<2>);
+    return reinterpret_cast<const void*>(rmb_small_kernel<0>);
+}
 
 }  // namespace rmb

@@ -146,7 +146,8 @@ def test_csr_generic_path_for_uniform_rows_not_vectorisable(k):
     mdp = mdpgen.csr_uniform_k(900, 3, k, gamma=0.9, seed=k)
     dm = rmb.DeviceMDP.from_host(mdp)
     ref = oracle.mbvi(mdp, 40, seed=1, eps=0.0, max_sweeps=3, traj=True)
-    for flags, path in ((rmb.RMB_FLAG_NO_CLUSTER, "csr-generic"), (0, "cluster")):
+    # uniform rows that are not vectorisable take the cluster path only when a state fits one lane per entry
+    for flags, path in ((rmb.RMB_FLAG_NO_CLUSTER, "csr-generic"), (0, "cluster" if 3 * k <= 32 else "csr-generic")):
         V, _, _, st = gpu_vi(dm, 40, 1, 0.0, 3, want_policy=False, flags=flags)
         assert st["path"] == path
         close(V, ref["traj"][2])
