@@ -171,8 +171,12 @@ typedef struct {
     int32_t path;            /* 0 dense, 1 CSR vectorised rows, 2 CSR generic rows, 3 dense TMA pipeline,
                                 4 one-cluster solve of a small MDP (RMB_FLAG_NO_CLUSTER) */
     int32_t lanes_per_state; /* CSR paths: lanes that share one state */
-    float ms;                /* device time of the call (CUDA events on `stream`) */
+    float ms;                /* device time of the call (CUDA events on `stream`); batched solves: this
+                                MDP's solve time (device clock, from its start to its group's first CTA
+                                finishing it) */
     int32_t batch;           /* the mini-batch size b used (the model's choice when opts.batch = 0) */
+    float start_ms;          /* batched solves: when this MDP started, after the first MDP of the launch
+                                started (device clock); 0 otherwise */
 } rmb_stats;
 
 /*

@@ -70,7 +70,7 @@ class rmb_stats(ctypes.Structure):
         ("sweeps", ctypes.c_int64), ("iters", ctypes.c_int64), ("barriers", ctypes.c_int64),
         ("residual", ctypes.c_double), ("v_shift", ctypes.c_double), ("status", ctypes.c_int32),
         ("grid_ctas", ctypes.c_int32), ("path", ctypes.c_int32), ("lanes_per_state", ctypes.c_int32),
-        ("ms", ctypes.c_float), ("batch", ctypes.c_int32),
+        ("ms", ctypes.c_float), ("batch", ctypes.c_int32), ("start_ms", ctypes.c_float),
     ]
 
     def as_dict(self):

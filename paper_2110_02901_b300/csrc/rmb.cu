@@ -1048,6 +1048,14 @@ int noalloc_scratch(void** out)
 //                steps = ceil(b / (states a group processes at once)); 13 GB/s = one SM's share of the
 //                measured P-stream rate
 //   time       = sweeps(b) * ceil(n/b) * batch time
+// MDPs with vectorised CSR rows and n <= kSoloSplitMaxN are solved with a copy of the values in every
+// CTA of the group (the first kSoloMaxN in shared memory, the rest in L2), where a step of the group's
+// lane groups costs the latency of its row loads.  Fitted to the per-MDP times of the 256-MDP bench
+// launch (one CTA per SM, all SMs busy): in state order (b = n) 0.84 us, 1.14 us with two chunks of a
+// state's rows per lane; in sigma's order 1.1 us, 1.37 us with two chunks, 1.5 us with two states per
+// warp; x(1 + 8 f) when a fraction f of the values is in L2, as nearly every step then waits for an
+// L2 gather.  A batch adds its barriers and the list exchange, 3 us (b = n) or 4 us:
+//   batch time = latency + steps * step_us
 // Each MDP gets the b minimising its time (unless the caller fixed b).  The makespan target M is
 // found by bisection: MDPs whose single-CTA time exceeds M get the smallest group that meets M, the
 // others are packed longest-first (LPT) onto the CTA that frees first, as the run-time queue does:
@@ -1057,6 +1065,8 @@ struct ItemCost {
     int64_t n;
     double bytes_per_state, gamma;
     int concurrency_per_cta;   // states one CTA processes at once
+    bool shared_values;        // solved with the values in shared memory (SoloRun)
+    bool two_chunks;           // a lane holds two chunks of a state's rows
 };
 
 double est_sweeps(double gamma, double eps, double frac)
@@ -1072,6 +1082,15 @@ double est_time_us(const ItemCost& c, int64_t b, int G, double eps)
     const double T = (double)((c.n + b - 1) / b);
     const double conc = (double)c.concurrency_per_cta * G;
     const double steps = std::ceil((double)b / conc);
+    if (c.shared_values) {
+        // states beyond kSoloMaxN read their values from L2
+        const double hi = c.n > kSoloMaxN ? (double)(c.n - kSoloMaxN) / (double)c.n : 0.0;
+        const double base = T > 1.0 ? (c.two_chunks ? 1.37 : (c.concurrency_per_cta > kCsrThreads / 32 ? 1.5 : 1.1))
+                                    : (c.two_chunks ? 1.14 : 0.84);
+        const double step_us = base * (1.0 + 8.0 * hi);
+        const double per_batch = (T > 1.0 ? 4.0 : 3.0) + steps * step_us;
+        return est_sweeps(c.gamma, eps, (double)b / (double)c.n) * T * per_batch;
+    }
     const double lat = G == 1 ? 1.2 : 5.0;
     const double stream = (double)b * c.bytes_per_state / (13000.0 * G);
     const double per_batch = lat + (steps * 2.0 > stream ? steps * 2.0 : stream);
@@ -1228,11 +1247,17 @@ int make_batch_plan(const rmb_batch_item* items, int count, const rmb_opts* O, i
         cs[i].gamma = M->gamma;
         cs[i].bytes_per_state = (double)M->m * (double)nnz_row * 8.0 + 4.0 * M->m;
         int lps = 32;
+        cs[i].shared_values = false;
+        cs[i].two_chunks = false;
         if (csr_vec_ok(M)) {
             const int k4 = M->k_uniform >> 2;
             const int cpr = k4 < 32 ? k4 : 32;
             const int all = pow2ceil(cpr * M->m);
             lps = all > 32 ? 32 : all;
+            // the batched kernel's fast rows (one or two chunks per lane, rows within one lane group)
+            const int nc = (k4 <= lps && (k4 & (k4 - 1)) == 0) ? (M->m * k4 + lps - 1) / lps : 0;
+            cs[i].shared_values = (nc == 1 || nc == 2) && M->n <= kSoloSplitMaxN;
+            cs[i].two_chunks = nc == 2;
         }
         cs[i].concurrency_per_cta = (kCsrThreads / 32) * (32 / lps);
         fixed[i] = items[i].batch;
@@ -1301,8 +1326,8 @@ int batched_ctas(int* ctas)
     DevInfo* D = nullptr;
     int st = dev_info(&D);
     if (st) return st;
-    // single-CTA MDPs of up to kSoloMaxN states keep their values in kSoloMaxN * 4 bytes of dynamic
-    // shared memory (SoloRun); the rest of the unified L1 stays cache
+    // MDPs of up to kSoloMaxN states keep their values in kSoloMaxN * 4 bytes of dynamic shared memory
+    // of every CTA that solves them (SoloRun); the rest of the unified L1 stays cache
     if (cudaFuncSetAttribute(batched_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, kSoloMaxN * 4) !=
         cudaSuccess)
         return RMB_ERR_CUDA;
@@ -1425,6 +1450,8 @@ int rmb_batched_results(const rmb_batch_handle* h, rmb_stats* out, void* stream)
                    cudaMemcpyDeviceToHost) != cudaSuccess)
         return RMB_ERR_CUDA;
     int worst = RMB_OK;
+    unsigned long long t0 = ~0ull;
+    for (int i = 0; i < h->count; ++i) t0 = c[i].t_begin < t0 ? c[i].t_begin : t0;
     for (int i = 0; i < h->count; ++i) {
         std::memset(&out[i], 0, sizeof(rmb_stats));
         out[i].sweeps = c[i].sweeps;
@@ -1434,6 +1461,8 @@ int rmb_batched_results(const rmb_batch_handle* h, rmb_stats* out, void* stream)
         out[i].v_shift = c[i].mu;
         out[i].status = c[i].status != 0 ? c[i].status : c[i].error;
         out[i].path = -1;
+        out[i].ms = (float)((double)(c[i].t_end - c[i].t_begin) * 1e-6);
+        out[i].start_ms = (float)((double)(c[i].t_begin - t0) * 1e-6);
         if (out[i].status != RMB_OK && worst == RMB_OK) worst = out[i].status;
     }
     return worst;

@@ -44,6 +44,9 @@ enum Path { PATH_DENSE = 0, PATH_CSR_VEC = 1, PATH_CSR_GEN = 2, PATH_DENSE_TMA =
 enum Kind { K_MIN = 0, K_POLICY = 1, K_GREEDY = 2 };
 
 constexpr int kCsrThreads = 512;
+constexpr int kSoloMaxN = 57344;        // batched MDPs up to this n keep their values in shared memory
+                                        // (SoloRun): 224 KB of the batched launch
+constexpr int kSoloSplitMaxN = 81920;   // ... up to this n the first kSoloMaxN of them (SPLIT)
 // cumulative weights of RMB_SELECT_WEIGHTED: tiles of 8192 weights (1024 threads x 8)
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 8;
@@ -535,27 +538,38 @@ __device__ __forceinline__ float lds_f32(uint32_t saddr)
     return v;
 }
 
-// a successor value from the values A: global memory (L1-cached, see gather), or, with SM, A is in
-// this CTA's shared memory
-template <bool SM>
-__device__ __forceinline__ float gather_v(const float* __restrict__ A, int j, uint32_t nm1)
+// Where the successor values live: global memory (L1-cached, see gather), this CTA's shared memory,
+// or split: states [0, nsm) in shared memory and the rest in global memory H (read from L2).
+enum ValueMem { VM_GLOBAL = 0, VM_SHARED = 1, VM_SPLIT = 2 };
+
+template <int VM>
+__device__ __forceinline__ float gather_v(const float* __restrict__ A, int j, uint32_t nm1, const float* H,
+                                          uint32_t nsm)
 {
-    if (SM) return lds_f32((uint32_t)__cvta_generic_to_shared(A) + 4u * min((uint32_t)j, nm1));
+    if (VM == VM_SHARED) return lds_f32((uint32_t)__cvta_generic_to_shared(A) + 4u * min((uint32_t)j, nm1));
+    if (VM == VM_SPLIT) {
+        // one generic load for either space (the cache operator applies to the global part only)
+        const uint32_t jj = min((uint32_t)j, nm1);
+        const float* q = (jj < nsm ? A : H) + jj;
+        float v;
+        asm volatile("ld.cg.f32 %0, [%1];" : "=f"(v) : "l"(q));
+        return v;
+    }
     return gather(A, j, nm1);
 }
 
 // min (and, with ARG, the lowest arg-min and the second smallest value) over the state's rows of
 // c + gamma * sum p * A[col]; every lane of the group gets the result
-template <bool ARG, int NC, bool SM = false>
+template <bool ARG, int NC, int VM = VM_GLOBAL>
 __device__ __forceinline__ Best fast_eval(const KP& p, const StateRegs<NC>& R, const float* __restrict__ A, int lps,
-                                          int lane_g)
+                                          int lane_g, const float* H = nullptr, uint32_t nsm = 0)
 {
     const uint32_t nm1 = (uint32_t)(p.n - 1);
     float part[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        const float g0 = gather_v<SM>(A, R.c[c].x, nm1), g1 = gather_v<SM>(A, R.c[c].y, nm1);
-        const float g2 = gather_v<SM>(A, R.c[c].z, nm1), g3 = gather_v<SM>(A, R.c[c].w, nm1);
+        const float g0 = gather_v<VM>(A, R.c[c].x, nm1, H, nsm), g1 = gather_v<VM>(A, R.c[c].y, nm1, H, nsm);
+        const float g2 = gather_v<VM>(A, R.c[c].z, nm1, H, nsm), g3 = gather_v<VM>(A, R.c[c].w, nm1, H, nsm);
         part[c] = fmaf(R.p[c].x, g0, fmaf(R.p[c].y, g1, fmaf(R.p[c].z, g2, R.p[c].w * g3)));
     }
     const int k4 = 1 << p.k4_log2;
@@ -1655,23 +1669,48 @@ struct Runner {
 };
 
 // ------------------------------------------------------------------------------------------------
-// MB-VI of one CSR MDP (vectorised rows) on one CTA with the values in its shared memory (a queue task
-// of the batched launch).  The same state arithmetic as Runner (fast_load / fast_eval, the same lanes
-// per state, centred values, the same re-centring), so results equal rmb_vi's grid solve bit for bit;
-// successor values come from shared memory instead of L2.  One buffer suffices: a batch's states read
-// the values from before the batch, their (state, value) pairs go to the workspace lists S / W, and a
-// CTA barrier later they are written into the values.
+// MB-VI of one CSR MDP (vectorised rows) by a group of CTAs of the batched launch, each CTA with a
+// private copy of all n values in its shared memory.  The same state arithmetic as Runner (fast_load /
+// fast_eval, the same lanes per state and the same split of a batch over the group, centred values,
+// the same re-centring), so results equal rmb_vi's grid solve bit for bit; successor values come from
+// shared memory instead of L2.  A batch's states read the values from before the batch (eq. (11)):
+// their (state, value) pairs go to the workspace lists S / W[t & 1], and after the group's barrier
+// every CTA writes the whole list into its copy.  The lists alternate from batch to batch, across
+// sweeps too: a CTA writes a list again two batches later, after the barrier of the batch between,
+// which every CTA reaches only after it has applied the list.  A one-CTA group uses CTA barriers only.
+// SPLIT: n is larger than the shared memory holds; states [nsm, n) keep their values in global memory
+// (read from L2), in one of two buffers.  Every CTA writes every entry of a list into that part too, so
+// a CTA's own writes complete it before its next batch reads it, and the writes of other CTAs store
+// the same values; a re-centring writes the shifted values into the other buffer (the same values
+// from every CTA), which the next shift two sweeps later overwrites only after every CTA has crossed
+// a barrier that follows its last read of it.
 // ------------------------------------------------------------------------------------------------
-template <int NCA>
+template <int NCA, bool SPLIT = false>
 struct SoloRun {
     const KP& p;
     RedSmem& rs;
-    float* Vs;          // n centred values (shared memory)
+    float* Vs;          // centred values of states [0, nsm) (shared memory)
+    uint32_t nsm;       // states whose values are in shared memory (n unless SPLIT)
+    int hb = 0;         // SPLIT: the global buffer p.d[hb] that holds states [nsm, n)
+    GroupView gv;
+    Ctrl* c;
+    bool lead;          // thread 0 of the group's first CTA
     Centre C;
     long long syncs = 0;
+    unsigned long long target = 0;
+    int red_epoch = 0;
     bool perm_ok = true;
 
-    __device__ SoloRun(const KP& kp, RedSmem& r, float* v) : p(kp), rs(r), Vs(v) {}
+    __device__ SoloRun(const KP& kp, RedSmem& r, float* v, GroupView g)
+        : p(kp), rs(r), Vs(v), nsm(SPLIT ? (uint32_t)kSoloMaxN : (uint32_t)kp.n), gv(g), c(kp.ctrl),
+          lead(g.rank == 0 && threadIdx.x == 0) {}
+
+    __device__ float val(int i) const { return (!SPLIT || (uint32_t)i < nsm) ? Vs[i] : ld_l2(p.d[hb] + i); }
+    __device__ void set_val(int i, float v)
+    {
+        if (!SPLIT || (uint32_t)i < nsm) Vs[i] = v;
+        else st_l2(p.d[hb] + i, v);
+    }
 
     __device__ PermKey key_for(long long k) const
     {
@@ -1695,6 +1734,19 @@ struct SoloRun {
         ++syncs;
         __syncthreads();
     }
+
+    // the group's barrier (a CTA barrier for a one-CTA group); false: a CTA reported an error or the
+    // wait timed out
+    __device__ bool gsync(int site)
+    {
+        ++syncs;
+        if (!perm_ok) atomicCAS(&c->error, 0, RMB_ERR_UNSUPPORTED);
+        grid_arrive(c, target, false, gv.size);
+        return grid_wait_arrived(c, target, p.timeout_ns, site, gv.size);
+    }
+
+    __device__ int gtid() const { return gv.rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ int gthreads() const { return gv.size * (int)blockDim.x; }
 
     // block-wide max |change|, min, max of the accumulators (every thread gets them)
     __device__ void reduce(Acc& a)
@@ -1729,34 +1781,43 @@ struct SoloRun {
         __syncthreads();
     }
 
-    // positions [pos0, pos0 + len) of the order K (K null: natural order): KIND K_MIN writes (state,
-    // value) into S / W[i]; K_GREEDY writes the outputs.  Rows load one step ahead (as csr_batch_fast).
+    // the state of step j of this lane group (-1 past the end); bs caches the resolved block of steps
+    __device__ int step_state(const FastGeom& G, int j, int pos0, int len, const PermKey* K, int& bs, int& bs_j0)
+    {
+        if (G.first + j * G.U >= len) return -1;
+        const int j0 = j - j % G.per_block;
+        if (j0 != bs_j0) {
+            bs = G.resolve(j0, pos0, len, K, &perm_ok);
+            bs_j0 = j0;
+        }
+        return __shfl_sync(0xffffffffu, bs, (j % G.per_block) * G.spw + G.g);
+    }
+
+    // this CTA's share of positions [pos0, pos0 + len) of the order K (K null: natural order): KIND
+    // K_MIN writes (state, value) into S / W[i] (i: the position in the batch); K_GREEDY writes the
+    // outputs.  Rows load two steps ahead.
     template <int KIND>
-    __device__ void batch(int pos0, int len, const PermKey* K, Acc& acc)
+    __device__ void batch(int pos0, int len, const PermKey* K, int32_t* S, float* W, Acc& acc)
     {
         constexpr bool ARG = (KIND == K_GREEDY);
-        const GroupView gv{0, 1};
         const int lps = p.lps_all;
         const FastGeom G(lps, gv);
         if (G.first >= len) return;
-        int block_states = G.resolve(0, pos0, len, K, &perm_ok);
-        int s_cur = __shfl_sync(0xffffffffu, block_states, G.g);
-        StateRegs<NCA> cur, nxt;
+        int bs = 0, bs_j0 = -1;
+        int s_cur = step_state(G, 0, pos0, len, K, bs, bs_j0);
+        int s_n1 = step_state(G, 1, pos0, len, K, bs, bs_j0);
+        StateRegs<NCA> cur, n1, n2;
         fast_load<K_MIN, NCA>(p, s_cur < 0 ? 0 : s_cur, s_cur >= 0, lps, G.lane_g, cur);
+        fast_load<K_MIN, NCA>(p, s_n1 < 0 ? 0 : s_n1, s_n1 >= 0, lps, G.lane_g, n1);
         for (int j = 0; G.first + j * G.U < len; ++j) {
-            const int jn = j + 1;
-            int s_nxt = -1;
-            if (G.first + jn * G.U < len) {
-                if (jn % G.per_block == 0) block_states = G.resolve(jn, pos0, len, K, &perm_ok);
-                s_nxt = __shfl_sync(0xffffffffu, block_states, (jn % G.per_block) * G.spw + G.g);
-            }
-            fast_load<K_MIN, NCA>(p, s_nxt < 0 ? 0 : s_nxt, s_nxt >= 0, lps, G.lane_g, nxt);
-            const bool lead = s_cur >= 0 && G.lane_g == 0;
-            const Best r = fast_eval<ARG, NCA, true>(p, cur, Vs, lps, G.lane_g);
-            if (lead) {
-                const float old = Vs[s_cur];
+            const int s_n2 = step_state(G, j + 2, pos0, len, K, bs, bs_j0);
+            fast_load<K_MIN, NCA>(p, s_n2 < 0 ? 0 : s_n2, s_n2 >= 0, lps, G.lane_g, n2);
+            const Best r = SPLIT ? fast_eval<ARG, NCA, VM_SPLIT>(p, cur, Vs, lps, G.lane_g, p.d[hb], nsm)
+                                 : fast_eval<ARG, NCA, VM_SHARED>(p, cur, Vs, lps, G.lane_g);
+            if (s_cur >= 0 && G.lane_g == 0) {
+                const float old = val(s_cur);
                 const float v = new_value(r.q, C);
-                if (v != v) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
+                if (v != v) atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
                 acc.dmax = fmaxf(acc.dmax, fabsf(v - old));
                 if (KIND == K_GREEDY) {
                     if (p.pi) st_l2(p.pi + s_cur, r.a);
@@ -1766,12 +1827,33 @@ struct SoloRun {
                     acc.vlo = fminf(acc.vlo, v);
                     acc.vhi = fmaxf(acc.vhi, v);
                     const int i = G.first + G.g + j * G.U;
-                    st_l2(p.S[0] + i, s_cur);
-                    st_l2(p.W[0] + i, v);
+                    st_l2(S + i, s_cur);
+                    st_l2(W + i, v);
                 }
             }
-            cur = nxt;
-            s_cur = s_nxt;
+            cur = n1;
+            n1 = n2;
+            s_cur = s_n1;
+            s_n1 = s_n2;
+        }
+    }
+
+    // write a batch's (state, value) list into this CTA's values: four pairs per thread in flight
+    __device__ void apply_list(const int32_t* S, const float* W, int len)
+    {
+        const int nt = blockDim.x;
+        for (int i0 = threadIdx.x; i0 < len; i0 += 4 * nt) {
+            int st[4];
+            float w[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 + u * nt;
+                st[u] = i < len ? ld_l2(S + i) : -1;
+                w[u] = i < len ? ld_l2(W + i) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (st[u] >= 0) set_val(st[u], w[u]);
         }
     }
 
@@ -1784,10 +1866,26 @@ struct SoloRun {
         return mid;
     }
 
+    __device__ void finish(long long sweeps, double residual, bool ok, bool converged)
+    {
+        if (!perm_ok) atomicCAS(&c->error, 0, RMB_ERR_UNSUPPORTED);
+        __syncthreads();
+        if (lead) {
+            c->sweeps = sweeps;
+            c->iters = 0;
+            c->barriers = syncs;
+            c->residual = residual;
+            c->mu = C.mu;
+            int st = ld_volatile(&c->error);
+            if (st == 0 && ok && !converged) st = RMB_ERR_NOT_CONVERGED;
+            c->status = st;
+        }
+    }
+
     __device__ void run()
     {
-        Ctrl* c = p.ctrl;
         if (ld_volatile(&c->error) != 0) return;
+        // set-up: every CTA reads all start values (the same centre in each)
         Acc a0 = {0.f, kInf, -kInf};
         for (int i = threadIdx.x; i < p.n; i += blockDim.x) {
             const float v = p.Vin[i];
@@ -1798,33 +1896,54 @@ struct SoloRun {
         reduce(a0);
         const double mu0 = (double)(float)(0.5 * ((double)a0.vlo + (double)a0.vhi));
         C = make_centre(mu0, p.gamma_d);
-        for (int i = threadIdx.x; i < p.n; i += blockDim.x) Vs[i] = (float)((double)p.Vin[i] - mu0);
+        for (int i = threadIdx.x; i < p.n; i += blockDim.x) set_val(i, (float)((double)p.Vin[i] - mu0));
         bar();
         long long sweeps = 0;
         double residual = 0.0;
         bool converged = false, ok = ld_volatile(&c->error) == 0;
         const bool ordered = p.T > 1;
+        const bool multi = gv.size > 1;
+        unsigned nbatch = 0;   // batches done (the list parity)
         for (long long j = 0; ok && j < p.max_sweeps; ++j) {
             const long long k = p.start_sweep + j;
             PermKey K = key_for(k);
-            if (p.perm_buf) {   // the whole order of the sweep, then the batches read it
-                for (int i = threadIdx.x; i < p.n; i += blockDim.x)
+            if (p.perm_buf && ordered) {
+                // the whole order of the sweep, then the batches read it (the group's last barrier of
+                // the previous sweep ordered every read of the previous order before these writes)
+                for (int i = gtid(); i < p.n; i += gthreads())
                     st_l2(p.perm_buf + i, order_at((uint32_t)i, K, &perm_ok));
-                bar();
+                if (!gsync(40)) { ok = false; break; }
                 K.buf = p.perm_buf;
             }
+            const int slot = red_epoch % 3;
+            if (multi && lead) {
+                const int nxt = (red_epoch + 1) % 3;
+                c->red_delta[nxt] = 0u;
+                c->red_hi[nxt] = 0u;
+                c->red_nlo[nxt] = 0u;
+            }
+            ++red_epoch;
             Acc acc = {0.f, kInf, -kInf};
-            for (int t = 0; t < p.T; ++t) {
+            for (int t = 0; ok && t < p.T; ++t) {
                 const int len = (t == p.T - 1) ? p.last_len : p.b;
-                batch<K_MIN>(t * p.b, len, ordered ? &K : nullptr, acc);
-                bar();
-                for (int i = threadIdx.x; i < len; i += blockDim.x) Vs[ld_l2(p.S[0] + i)] = ld_l2(p.W[0] + i);
+                const int par = multi ? (int)(nbatch++ & 1u) : 0;
+                int32_t* S = p.S[par];
+                float* W = p.W[par];
+                batch<K_MIN>(t * p.b, len, ordered ? &K : nullptr, S, W, acc);
+                if (multi && t == p.T - 1) publish(c, slot, acc, rs);
+                if (!gsync(41)) { ok = false; break; }
+                apply_list(S, W, len);
                 bar();
             }
-            reduce(acc);
+            if (!ok) break;
+            if (multi) {
+                read_slot(c, slot, rs, acc.dmax, acc.vlo, acc.vhi);
+            } else {
+                reduce(acc);
+            }
             ++sweeps;
             residual = (double)acc.dmax;
-            if (threadIdx.x == 0 && p.trace) p.trace[j] = residual;
+            if (lead && p.trace) p.trace[j] = residual;
             if (acc.dmax != acc.dmax) {
                 atomicCAS(&c->error, 0, RMB_ERR_NONFINITE);
                 ok = false;
@@ -1841,7 +1960,12 @@ struct SoloRun {
             // the grid solve ends its last sweep without re-centring; so does this one (same outputs)
             const float sh = j + 1 < p.max_sweeps ? shift_for(acc.vlo, acc.vhi) : 0.f;
             if (sh != 0.f) {
-                for (int i = threadIdx.x; i < p.n; i += blockDim.x) Vs[i] -= sh;
+                for (int i = threadIdx.x; i < (int)nsm; i += blockDim.x) Vs[i] -= sh;
+                if (SPLIT) {
+                    for (int i = (int)nsm + threadIdx.x; i < p.n; i += blockDim.x)
+                        st_l2(p.d[hb ^ 1] + i, ld_l2(p.d[hb] + i) - sh);
+                    hb ^= 1;
+                }
                 C = make_centre(C.mu + (double)sh, p.gamma_d);
                 bar();
             }
@@ -1849,23 +1973,12 @@ struct SoloRun {
         if (ok) {
             if (p.pi || p.qgap) {
                 Acc g = {0.f, kInf, -kInf};
-                batch<K_GREEDY>(0, p.n, nullptr, g);
+                batch<K_GREEDY>(0, p.n, nullptr, nullptr, nullptr, g);
             } else {
-                for (int i = threadIdx.x; i < p.n; i += blockDim.x) p.Vout[i] = (float)(C.mu + (double)Vs[i]);
+                for (int i = gtid(); i < p.n; i += gthreads()) p.Vout[i] = (float)(C.mu + (double)val(i));
             }
         }
-        if (!perm_ok) atomicCAS(&c->error, 0, RMB_ERR_UNSUPPORTED);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            c->sweeps = sweeps;
-            c->iters = 0;
-            c->barriers = syncs;
-            c->residual = residual;
-            c->mu = C.mu;
-            int st = ld_volatile(&c->error);
-            if (st == 0 && ok && !converged) st = RMB_ERR_NOT_CONVERGED;
-            c->status = st;
-        }
+        finish(sweeps, residual, ok, converged);
     }
 };
 
@@ -1891,7 +2004,5 @@ const void* small_kernel_ptr(int nc);                // rmb_small_kernel<NC> (on
 constexpr int kSmallThreads = 512;
 constexpr int kSmallMaxPer = 2;                      // states per warp and batch in rmb_small_kernel
 constexpr int kSmallMaxDyn = 220 * 1024;             // its dynamic shared memory: 16 bytes per state + 16
-constexpr int kSoloMaxN = 40960;                     // batched queue tasks up to this n keep their values in
-                                                     // shared memory (SoloRun): 160 KB of the batched launch
 
 }  // namespace rmb

@@ -62,14 +62,24 @@ rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off,
         if (threadIdx.x == 0) s_kp = kps[bt.item];
         __syncthreads();
         const GroupView gv{bt.rank, bt.size};
-        // an MDP solved by this CTA alone keeps its values in shared memory when they fit
-        const bool solo = bt.size == 1 && s_kp.path == PATH_CSR_VEC && s_kp.n <= kSoloMaxN && s_kp.select == 0 &&
-                          s_kp.residual_kind == 0 && (s_kp.flags & RMB_FLAG_ASYNC) == 0;
-        if (solo && s_kp.nc_all == 1) {
-            SoloRun<1> R(s_kp, rs, solo_values);
+        const unsigned long long t_begin = globaltimer_ns();
+        // every CTA of the group keeps a copy of the values in its shared memory when they fit (the
+        // launch is MB-VI over sigma with the sweep stop test only)
+        // (the first kSoloMaxN values when they do not)
+        const bool solo = s_kp.path == PATH_CSR_VEC && s_kp.n <= kSoloSplitMaxN && s_kp.mode == MODE_VI &&
+                          s_kp.select == 0 && s_kp.residual_kind == 0 && (s_kp.flags & RMB_FLAG_ASYNC) == 0;
+        const bool split = s_kp.n > kSoloMaxN;
+        if (solo && !split && s_kp.nc_all == 1) {
+            SoloRun<1> R(s_kp, rs, solo_values, gv);
+            R.run();
+        } else if (solo && !split && s_kp.nc_all == 2) {
+            SoloRun<2> R(s_kp, rs, solo_values, gv);
+            R.run();
+        } else if (solo && s_kp.nc_all == 1) {
+            SoloRun<1, true> R(s_kp, rs, solo_values, gv);
             R.run();
         } else if (solo && s_kp.nc_all == 2) {
-            SoloRun<2> R(s_kp, rs, solo_values);
+            SoloRun<2, true> R(s_kp, rs, solo_values, gv);
             R.run();
         } else if (s_kp.path == PATH_CSR_VEC && s_kp.nc_all == 1 && s_kp.nc_one == 1) {
             Runner<PATH_CSR_VEC, 1, 1> R(s_kp, rs, nullptr, nullptr, gv);
@@ -80,6 +90,10 @@ rmb_batched_kernel(const KP* __restrict__ kps, const int* __restrict__ task_off,
         } else {
             Runner<PATH_CSR_GEN> R(s_kp, rs, nullptr, nullptr, gv);
             R.run();
+        }
+        if (threadIdx.x == 0 && bt.rank == 0) {
+            s_kp.ctrl->t_begin = t_begin;
+            s_kp.ctrl->t_end = globaltimer_ns();
         }
     }
 }

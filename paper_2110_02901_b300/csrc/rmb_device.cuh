@@ -181,6 +181,7 @@ struct Ctrl {
     long long sweeps, iters, barriers;
     double residual, mu;
     int status, pad;
+    unsigned long long t_begin, t_end;   // batched solves: globaltimer at the MDP's start and end (ns)
 };
 
 // The CTAs that solve one MDP: all of the grid (single solves) or a group of it (batched solves).

@@ -338,7 +338,7 @@ struct SmallRun {
     __device__ Best compute(const Ahead& h, const AheadVec<NC>& hv, const float* A) const
     {
         const int lane = threadIdx.x & 31;
-        if constexpr (NC > 0) return fast_eval<ARG, NC, true>(p, hv.R, A, 32, lane);
+        if constexpr (NC > 0) return fast_eval<ARG, NC, VM_SHARED>(p, hv.R, A, 32, lane);
         if (!h.fast) return eval<ARG>(h.s, A);
         Best cur = {kInf, 0x7fffffff, kInf};
         if (p.path == PATH_DENSE) {
