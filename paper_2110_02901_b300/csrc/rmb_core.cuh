@@ -504,7 +504,28 @@ struct Carry {
     bool valid;
 };
 
-template <int KIND, int NC>
+// Row loads that keep their place in the program: volatile, so the compiler issues them where they are
+// written (ahead of the gathers of earlier steps) instead of next to their first use.
+__device__ __forceinline__ float4 ld_pinned_cs(const float4* a)
+{
+    float4 v;
+    asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a));
+    return v;
+}
+__device__ __forceinline__ int4 ld_pinned_cs(const int4* a)
+{
+    int4 v;
+    asm volatile("ld.global.cs.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a));
+    return v;
+}
+__device__ __forceinline__ float ld_pinned_nc(const float* a)
+{
+    float v;
+    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(a));
+    return v;
+}
+
+template <int KIND, int NC, bool PINNED = false>
 __device__ __forceinline__ void fast_load(const KP& p, int s, bool act, int lps, int lane_g, StateRegs<NC>& R)
 {
     int pi_s = -1;
@@ -519,7 +540,11 @@ __device__ __forceinline__ void fast_load(const KP& p, int s, bool act, int lps,
         const int ch = ci - (row << p.k4_log2);
         const int a = KIND == K_POLICY ? pi_s : row;
         const int64_t r = (int64_t)s * p.m + a;
-        if (v) {
+        if (v && PINNED) {
+            R.p[c] = ld_pinned_cs(reinterpret_cast<const float4*>(p.prob + r * p.k) + ch);
+            R.c[c] = ld_pinned_cs(reinterpret_cast<const int4*>(p.col + r * p.k) + ch);
+            R.cost[c] = ld_pinned_nc(p.cost + r);
+        } else if (v) {
             R.p[c] = __ldcs(reinterpret_cast<const float4*>(p.prob + r * p.k) + ch);
             R.c[c] = __ldcs(reinterpret_cast<const int4*>(p.col + r * p.k) + ch);
             R.cost[c] = __ldg(p.cost + r);
@@ -779,17 +804,24 @@ __device__ __forceinline__ void decode16(const uint4 w, float* d)
             d[2 * i + 1] = __uint_as_float(u[i] & 0xffff0000u);
         }
     } else {
+        // e4m3 pairs to f16 pairs (exact), then each f16 to f32 (exact): three conversions per 4 bytes
         const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u[i] & 0xffffu), __NV_E4M3);
-            const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(u[i] >> 16), __NV_E4M3);
-            const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
-            const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
-            d[4 * i] = a.x;
-            d[4 * i + 1] = a.y;
-            d[4 * i + 2] = b.x;
-            d[4 * i + 3] = b.y;
+            uint32_t h01, h23;
+            asm("{ .reg .b16 lo, hi;\n\t"
+                "mov.b32 {lo, hi}, %2;\n\t"
+                "cvt.rn.f16x2.e4m3x2 %0, lo;\n\t"
+                "cvt.rn.f16x2.e4m3x2 %1, hi; }"
+                : "=r"(h01), "=r"(h23) : "r"(u[i]));
+            asm("{ .reg .b16 a, b, c, e;\n\t"
+                "mov.b32 {a, b}, %4;\n\t"
+                "mov.b32 {c, e}, %5;\n\t"
+                "cvt.f32.f16 %0, a;\n\t"
+                "cvt.f32.f16 %1, b;\n\t"
+                "cvt.f32.f16 %2, c;\n\t"
+                "cvt.f32.f16 %3, e; }"
+                : "=f"(d[4 * i]), "=f"(d[4 * i + 1]), "=f"(d[4 * i + 2]), "=f"(d[4 * i + 3]) : "r"(h01), "r"(h23));
         }
     }
 }
@@ -960,13 +992,16 @@ __device__ bool dense_batch(const KP& p, const GroupView& gv, DenseSmem& sm, flo
 // ------------------------------------------------------------------------------------------------
 // Dense path with a TMA pipeline: one producer warp streams the transition rows of the CTA's states,
 // row group by row group and column tile by column tile, into a ring of shared-memory stages with
-// cp.async.bulk (mbarrier transaction counts); eight consumer warps decode them and multiply with the
+// cp.async.bulk (mbarrier transaction counts); consumer warps decode them and multiply with the
 // current values, staged once per batch.  Memory-level parallelism is the ring (kRingStages x
 // kStageBytes per SM), not registers, so coded rows (bf16 / fp8) stream as fast as float32 rows.
+// The consumers never wait for each other: each writes its partial row sums of a row group into one of
+// two slots and arrives on the slot's mbarrier; a reducer warp sums the slots, forms Q(s, a), and
+// finishes each state (min over actions, new value), then frees the slot.
 // Every wait is bounded; after a timeout all threads still pass the same barriers (abort flag).
 // ------------------------------------------------------------------------------------------------
-constexpr int kTmaConsumers = 8;                    // consumer warps
-constexpr int kTmaThreads = (kTmaConsumers + 1) * 32;
+constexpr int kTmaConsumers = 16;                   // consumer warps
+constexpr int kTmaThreads = (kTmaConsumers + 2) * 32;   // + the producer warp and the reducer warp
 constexpr int kRingStages = 2;
 constexpr int kStageBytes = 65536;
 constexpr int kTmaRowGroup = 8;                     // rows per stage (all-action passes)
@@ -975,12 +1010,14 @@ constexpr int kTmaMaxStates = 512;                  // states per chunk of a bat
 struct TmaSmem {
     uint64_t full[kRingStages];
     uint64_t empty[kRingStages];
+    uint64_t red_full[2];    // a slot's partial sums are written (one arrival per consumer warp)
+    uint64_t red_empty[2];   // the reducer has read the slot
     uint64_t vbar;
     uint32_t vphase;
     int abort;
     int ids[kTmaMaxStates];
     int pis[kTmaMaxStates];
-    float red[kTmaConsumers][kTmaRowGroup];
+    float red[2][kTmaConsumers][kTmaRowGroup];
     float q[kDenseMaxM];
 };
 
@@ -1011,18 +1048,19 @@ __device__ __forceinline__ bool mb_wait(uint32_t mb, uint32_t parity, const KP& 
     return true;
 }
 
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kTmaConsumers * 32) : "memory"); }
 
 template <int KIND, int DT>
 __device__ bool dense_batch_tma(const KP& p, const GroupView& gv, TmaSmem& sm, float* vst, unsigned char* ring,
-                                uint32_t& ring_it, const float* A, float* B, int pos0, int len, const PermKey* K,
-                                int32_t* Sout, float* Wout, const Centre& C, Acc& acc, bool* perm_ok)
+                                uint32_t& ring_it, uint32_t& red_it, const float* A, float* B, int pos0, int len,
+                                const PermKey* K, int32_t* Sout, float* Wout, const Centre& C, Acc& acc,
+                                bool* perm_ok)
 {
     constexpr int EB = Elem<DT>::bytes;
     constexpr int E = Elem<DT>::per16;
     const int n = p.n;
     const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
     const bool producer = wid == kTmaConsumers;
+    const bool reducer = wid == kTmaConsumers + 1;
     const int RG = KIND == K_POLICY ? 1 : kTmaRowGroup;
     const int nrows = KIND == K_POLICY ? 1 : p.m;
     const int TC = min(n, (kStageBytes / (RG * EB)) & ~15);       // columns per tile
@@ -1101,10 +1139,44 @@ __device__ bool dense_batch_tma(const KP& p, const GroupView& gv, TmaSmem& sm, f
                     }
                 }
             }
-        } else {
-            uint32_t it = ring_it;
+        } else if (reducer) {
+            uint32_t rit = red_it;
             for (int i = 0; i < cnt; ++i) {
                 const int s = sm.ids[i];
+                bool all_ok = true;
+                for (int g = 0; g < ngroups; ++g, ++rit) {
+                    const int a0 = g * RG;
+                    const int rg = min(RG, nrows - a0);
+                    const int slot = (int)(rit & 1u);
+                    const bool ok = mb_wait((uint32_t)__cvta_generic_to_shared(&sm.red_full[slot]), (rit >> 1) & 1u, p,
+                                            abort_flag);
+                    all_ok = all_ok && ok;
+                    if (ok && lane < rg) {
+                        float tot = 0.f;
+                        for (int w = 0; w < kTmaConsumers; ++w) tot += sm.red[slot][w][lane];
+                        const int a = KIND == K_POLICY ? sm.pis[i] : a0 + lane;
+                        const int64_t r = (int64_t)s * p.m + a;
+                        if (DT != RMB_P_F32) tot *= __ldg(p.row_scale + r);
+                        const float c = __ldg(p.cost + r);
+                        sm.q[KIND == K_POLICY ? 0 : a0 + lane] = (c == kInf) ? kInf : fmaf(p.gamma, tot, c);
+                    }
+                    __syncwarp();
+                    if (lane == 0 && ok)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];"
+                                     ::"r"((uint32_t)__cvta_generic_to_shared(&sm.red_empty[slot])) : "memory");
+                }
+                if (lane == 0 && all_ok && !*abort_flag) {
+                    Best best = {kInf, 0x7fffffff, kInf};
+                    for (int ai = 0; ai < nrows; ++ai)
+                        best = better(best, Best{sm.q[ai], KIND == K_POLICY ? sm.pis[i] : ai, kInf});
+                    state_epilogue<KIND>(p, best, s, me + (c0 + i) * G, A, B, Sout, Wout, C, acc);
+                }
+                __syncwarp();
+            }
+        } else {
+            uint32_t rit = red_it;
+            uint32_t it = ring_it;
+            for (int i = 0; i < cnt; ++i) {
                 for (int g = 0; g < ngroups; ++g) {
                     const int a0 = g * RG;
                     const int rg = min(RG, nrows - a0);
@@ -1152,35 +1224,30 @@ __device__ bool dense_batch_tma(const KP& p, const GroupView& gv, TmaSmem& sm, f
                             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];"
                                          ::"r"((uint32_t)__cvta_generic_to_shared(&sm.empty[slot])) : "memory");
                     }
-                    // row sums over the consumer warps
+                    // this warp's row sums into the group's slot, once the reducer has freed it
 #pragma unroll
                     for (int r = 0; r < kTmaRowGroup; ++r) {
                         float x = accv[r];
                         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-                        if (lane == 0) sm.red[wid][r] = x;
+                        accv[r] = x;
                     }
-                    consumer_sync();
-                    if (tid < rg) {
-                        float tot = 0.f;
-                        for (int w = 0; w < kTmaConsumers; ++w) tot += sm.red[w][tid];
-                        const int a = KIND == K_POLICY ? sm.pis[i] : a0 + tid;
-                        const int64_t r = (int64_t)s * p.m + a;
-                        if (DT != RMB_P_F32) tot *= __ldg(p.row_scale + r);
-                        const float c = __ldg(p.cost + r);
-                        sm.q[KIND == K_POLICY ? 0 : a0 + tid] = (c == kInf) ? kInf : fmaf(p.gamma, tot, c);
+                    const int slot = (int)(rit & 1u);
+                    const uint32_t use = rit >> 1;
+                    const bool free_ok = use == 0 || mb_wait((uint32_t)__cvta_generic_to_shared(&sm.red_empty[slot]),
+                                                             (use - 1) & 1u, p, abort_flag);
+                    if (free_ok && lane == 0) {
+#pragma unroll
+                        for (int r = 0; r < kTmaRowGroup; ++r) sm.red[slot][wid][r] = accv[r];
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];"
+                                     ::"r"((uint32_t)__cvta_generic_to_shared(&sm.red_full[slot])) : "memory");
                     }
-                    consumer_sync();
-                }
-                if (tid == 0 && !*abort_flag) {
-                    Best best = {kInf, 0x7fffffff, kInf};
-                    for (int ai = 0; ai < nrows; ++ai)
-                        best = better(best, Best{sm.q[ai], KIND == K_POLICY ? sm.pis[i] : ai, kInf});
-                    state_epilogue<KIND>(p, best, s, me + (c0 + i) * G, A, B, Sout, Wout, C, acc);
+                    ++rit;
                 }
             }
         }
-        // every thread advances the ring counter by the tiles of this chunk
+        // every thread advances the ring and slot counters by the tiles and row groups of this chunk
         ring_it += (uint32_t)(cnt * ngroups * ntiles);
+        red_it += (uint32_t)(cnt * ngroups);
     }
     __syncthreads();
     return *abort_flag == 0;
@@ -1255,6 +1322,7 @@ struct Runner {
     TmaSmem* tsm = nullptr;        // dense TMA path: barriers, state lists
     unsigned char* ring = nullptr; // dense TMA path: stage ring
     uint32_t ring_it = 0;          // dense TMA path: tiles streamed so far (same in every thread)
+    uint32_t red_it = 0;           // dense TMA path: row groups reduced so far (same in every thread)
 
     __device__ Runner(const KP& kp, RedSmem& r, DenseSmem* d, float* st, GroupView g)
         : p(kp), c(kp.ctrl), target(0), barriers(0), stall(false), cur(0), red_epoch(0), rs(r), dsm(d),
@@ -1298,7 +1366,7 @@ struct Runner {
     {
         if (PATH == PATH_DENSE_TMA) {
             constexpr int DT = NCA;
-            return dense_batch_tma<KIND, DT>(p, gv, *tsm, stage, ring, ring_it, A, B, pos0, len, K, So, Wo, C, acc,
+            return dense_batch_tma<KIND, DT>(p, gv, *tsm, stage, ring, ring_it, red_it, A, B, pos0, len, K, So, Wo, C, acc,
                                              &perm_ok);
         }
         if (PATH == PATH_DENSE) {
@@ -1543,6 +1611,12 @@ struct Runner {
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->full[i])) : "memory");
                 asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->empty[i])),
                              "r"(kTmaConsumers) : "memory");
+            }
+            for (int i = 0; i < 2; ++i) {
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->red_full[i])),
+                             "r"(kTmaConsumers) : "memory");
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->red_empty[i]))
+                             : "memory");
             }
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&tsm->vbar)) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1807,11 +1881,11 @@ struct SoloRun {
         int s_cur = step_state(G, 0, pos0, len, K, bs, bs_j0);
         int s_n1 = step_state(G, 1, pos0, len, K, bs, bs_j0);
         StateRegs<NCA> cur, n1, n2;
-        fast_load<K_MIN, NCA>(p, s_cur < 0 ? 0 : s_cur, s_cur >= 0, lps, G.lane_g, cur);
-        fast_load<K_MIN, NCA>(p, s_n1 < 0 ? 0 : s_n1, s_n1 >= 0, lps, G.lane_g, n1);
+        fast_load<K_MIN, NCA, true>(p, s_cur < 0 ? 0 : s_cur, s_cur >= 0, lps, G.lane_g, cur);
+        fast_load<K_MIN, NCA, true>(p, s_n1 < 0 ? 0 : s_n1, s_n1 >= 0, lps, G.lane_g, n1);
         for (int j = 0; G.first + j * G.U < len; ++j) {
             const int s_n2 = step_state(G, j + 2, pos0, len, K, bs, bs_j0);
-            fast_load<K_MIN, NCA>(p, s_n2 < 0 ? 0 : s_n2, s_n2 >= 0, lps, G.lane_g, n2);
+            fast_load<K_MIN, NCA, true>(p, s_n2 < 0 ? 0 : s_n2, s_n2 >= 0, lps, G.lane_g, n2);
             const Best r = SPLIT ? fast_eval<ARG, NCA, VM_SPLIT>(p, cur, Vs, lps, G.lane_g, p.d[hb], nsm)
                                  : fast_eval<ARG, NCA, VM_SHARED>(p, cur, Vs, lps, G.lane_g);
             if (s_cur >= 0 && G.lane_g == 0) {
