@@ -38,8 +38,8 @@ EPS = 1e-6
 CSR_DRAM_BYTES_PER_STATE_PASS = (11167924480 + 10862336) / (21 * 262144)
 # batched launch: DRAM bytes (read + write) over the algorithmic row bytes, from one ncu capture of the
 # 256-MDP launch with every MDP capped at 20 sweeps (74.8343 GB + 0.4083 GB over 72.0046 GB)
-BATCHED_DRAM_PER_ALGO_BYTE = (74834331392 + 408346112) / 72004641408
-DENSE_DRAM_BYTES_PER_P_BYTE = (4285011968 + 3790336) / (4 * 4096 * 16 * 4096 * 4)
+BATCHED_DRAM_PER_ALGO_BYTE = (72708093000 + 150380800) / 72004641408
+DENSE_DRAM_BYTES_PER_P_BYTE = (4285076000 + 7139328) / (4 * 4096 * 16 * 4096 * 4)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]
 HEADLINE_B = 262144
 MPI_K = 10
@@ -810,7 +810,7 @@ def _dense16k(args, world, rmb, torch, stream, hbm, peak_kind):
                  roofline={"bound": "hbm", "achieved": best["p_stream_gbs"], "peak": hbm, "unit": "GB/s",
                            "frac": best["p_stream_gbs"] / hbm,
                            # 20 sweeps of P per launch x DRAM bytes per P byte of one ncu capture of this
-                           # kernel (n = 4096, 4 sweeps: 4.2889 GB for 4.2950 GB of P)
+                           # kernel (n = 4096, 4 sweeps: 4.2922 GB for 4.2950 GB of P)
                            "traffic": 20 * n * m * n * 4 * DENSE_DRAM_BYTES_PER_P_BYTE,
                            "traffic_note": "ncu capture at n=4096 scaled by P bytes",
                            "kernel": "rmb_dense_tma_kernel<f32>", "peak_kind": peak_kind},
@@ -905,7 +905,7 @@ def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
                            "frac": nnz_passes / (ms / 1e3) / 1e9 / hbm,
                            "traffic": BATCHED_DRAM_PER_ALGO_BYTE * nnz_passes,
                            "traffic_note": "ncu DRAM bytes / algorithmic bytes of the same launch capped at 20 "
-                                           "sweeps per MDP (1.045), times this run's algorithmic bytes",
+                                           "sweeps per MDP (1.012), times this run's algorithmic bytes",
                            "kernel": "rmb_batched_kernel", "peak_kind": peak_kind},
                  cpu_baseline=cpu)
 
