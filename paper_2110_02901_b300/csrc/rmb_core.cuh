@@ -617,14 +617,15 @@ __device__ __forceinline__ Best fast_eval(const KP& p, const StateRegs<NC>& R, c
 }
 
 struct FastGeom {
-    int lane, spw, per_block, g, lane_g, U, first, my_off, my_step;
+    int lane, spw, per_block, pb_mask, g, lane_g, U, first, my_off, my_step;
     __device__ FastGeom(int lps, const GroupView& gv)
     {
         lane = threadIdx.x & 31;
         const int warp = (gv.rank * (int)blockDim.x + (int)threadIdx.x) >> 5;
         const int nwarps = (gv.size * (int)blockDim.x) >> 5;
         spw = 32 / lps;
-        per_block = 32 / spw;          // steps covered by one permutation evaluation per lane
+        per_block = 32 / spw;          // steps covered by one permutation evaluation per lane (= lps)
+        pb_mask = per_block - 1;       // lps is a power of two: j % per_block = j & pb_mask
         g = lane / lps;
         lane_g = lane - g * lps;
         U = nwarps * spw;
@@ -679,8 +680,8 @@ __device__ void csr_batch_fast(const KP& p, const GroupView& gv, int lps, const 
         const int jn = j + 1;
         int s_nxt = -1;
         if (G.first + jn * G.U < len) {
-            if (jn % G.per_block == 0) block_states = G.resolve(jn, pos0, len, K, perm_ok);
-            s_nxt = __shfl_sync(0xffffffffu, block_states, (jn % G.per_block) * G.spw + G.g);
+            if ((jn & G.pb_mask) == 0) block_states = G.resolve(jn, pos0, len, K, perm_ok);
+            s_nxt = __shfl_sync(0xffffffffu, block_states, (jn & G.pb_mask) * G.spw + G.g);
         }
         fast_load<LK, NC>(p, s_nxt < 0 ? 0 : s_nxt, s_nxt >= 0, lps, G.lane_g, nxt);
         const bool lead = s_cur >= 0 && G.lane_g == 0;
@@ -1859,12 +1860,12 @@ struct SoloRun {
     __device__ int step_state(const FastGeom& G, int j, int pos0, int len, const PermKey* K, int& bs, int& bs_j0)
     {
         if (G.first + j * G.U >= len) return -1;
-        const int j0 = j - j % G.per_block;
+        const int j0 = j & ~G.pb_mask;
         if (j0 != bs_j0) {
             bs = G.resolve(j0, pos0, len, K, &perm_ok);
             bs_j0 = j0;
         }
-        return __shfl_sync(0xffffffffu, bs, (j % G.per_block) * G.spw + G.g);
+        return __shfl_sync(0xffffffffu, bs, (j & G.pb_mask) * G.spw + G.g);
     }
 
     // this CTA's share of positions [pos0, pos0 + len) of the order K (K null: natural order): KIND
@@ -1874,6 +1875,7 @@ struct SoloRun {
     __device__ void batch(int pos0, int len, const PermKey* K, int32_t* S, float* W, Acc& acc)
     {
         constexpr bool ARG = (KIND == K_GREEDY);
+        const float* Hs = SPLIT ? p.d[hb] : nullptr;
         const int lps = p.lps_all;
         const FastGeom G(lps, gv);
         if (G.first >= len) return;
@@ -1886,7 +1888,7 @@ struct SoloRun {
         for (int j = 0; G.first + j * G.U < len; ++j) {
             const int s_n2 = step_state(G, j + 2, pos0, len, K, bs, bs_j0);
             fast_load<K_MIN, NCA, true>(p, s_n2 < 0 ? 0 : s_n2, s_n2 >= 0, lps, G.lane_g, n2);
-            const Best r = SPLIT ? fast_eval<ARG, NCA, VM_SPLIT>(p, cur, Vs, lps, G.lane_g, p.d[hb], nsm)
+            const Best r = SPLIT ? fast_eval<ARG, NCA, VM_SPLIT>(p, cur, Vs, lps, G.lane_g, Hs, nsm)
                                  : fast_eval<ARG, NCA, VM_SHARED>(p, cur, Vs, lps, G.lane_g);
             if (s_cur >= 0 && G.lane_g == 0) {
                 const float old = val(s_cur);
