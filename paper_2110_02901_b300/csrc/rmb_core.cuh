@@ -597,21 +597,30 @@ __device__ __forceinline__ Best fast_eval(const KP& p, const StateRegs<NC>& R, c
         const float g2 = gather_v<VM>(A, R.c[c].z, nm1, H, nsm), g3 = gather_v<VM>(A, R.c[c].w, nm1, H, nsm);
         part[c] = fmaf(R.p[c].x, g0, fmaf(R.p[c].y, g1, fmaf(R.p[c].z, g2, R.p[c].w * g3)));
     }
-    const int k4 = 1 << p.k4_log2;
-    for (int off = 1; off < k4; off <<= 1) {
+    // the two butterfly stages as fixed five-level ladders with warp-uniform conditions (no loop
+    // counters): sums within a row (offsets < k4), then the minimum over rows (k4 <= offset < lps)
+    const int k4l = p.k4_log2;
 #pragma unroll
-        for (int c = 0; c < NC; ++c) part[c] += __shfl_xor_sync(0xffffffffu, part[c], off);
+    for (int l = 0; l < 5; ++l) {
+        if (l < k4l) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c) part[c] += __shfl_xor_sync(0xffffffffu, part[c], 1 << l);
+        }
     }
     Best b = {kInf, 0x7fffffff, kInf};
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const float q = R.cost[c] == kInf ? kInf : fmaf(p.gamma, part[c], R.cost[c]);
-        if (ARG) b = better(b, Best{q, (c * lps + lane_g) >> p.k4_log2, kInf});
+        if (ARG) b = better(b, Best{q, (c * lps + lane_g) >> k4l, kInf});
         else b.q = fminf(b.q, q);
     }
-    for (int off = k4; off < lps; off <<= 1) {
-        if (ARG) b = better(b, shfl_xor_best<true>(b, off));
-        else b.q = fminf(b.q, __shfl_xor_sync(0xffffffffu, b.q, off));
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        const int off = 1 << l;
+        if (l >= k4l && off < lps) {
+            if (ARG) b = better(b, shfl_xor_best<true>(b, off));
+            else b.q = fminf(b.q, __shfl_xor_sync(0xffffffffu, b.q, off));
+        }
     }
     return b;
 }
