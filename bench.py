@@ -37,7 +37,7 @@ N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
 CSR_DRAM_BYTES_PER_STATE_PASS = (11167924480 + 10862336) / (21 * 262144)
 # batched launch: DRAM bytes (read + write) over the algorithmic row bytes, from one ncu capture of the
-# 256-MDP launch with every MDP capped at 20 sweeps (74.8343 GB + 0.4083 GB over 72.0046 GB)
+# 256-MDP launch with every MDP capped at 20 sweeps (72.7081 GB + 0.1504 GB over 72.0046 GB)
 BATCHED_DRAM_PER_ALGO_BYTE = (72708093000 + 150380800) / 72004641408
 DENSE_DRAM_BYTES_PER_P_BYTE = (4285076000 + 7139328) / (4 * 4096 * 16 * 4096 * 4)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]

@@ -532,21 +532,23 @@ __device__ __forceinline__ void fast_load(const KP& p, int s, bool act, int lps,
     if (KIND == K_POLICY && act)
         pi_s = (int)min((uint32_t)ld_l2(p.pi_in ? p.pi_in + s : p.pi + s), (uint32_t)(p.m - 1));
     const int total = (KIND == K_POLICY ? 1 : p.m) << p.k4_log2;
+    // the loaded rows are contiguous, k = 4 k4 entries each: chunk ci of them starts 4 ci entries
+    // after the first row's start, and belongs to row ci >> log2 k4
+    const int64_t r0 = (int64_t)s * p.m + (KIND == K_POLICY ? pi_s : 0);
+    const int64_t e0 = r0 * p.k;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int ci = c * lps + lane_g;
         const bool v = act && ci < total;
-        const int row = ci >> p.k4_log2;
-        const int ch = ci - (row << p.k4_log2);
-        const int a = KIND == K_POLICY ? pi_s : row;
-        const int64_t r = (int64_t)s * p.m + a;
+        const int64_t e = e0 + 4 * ci;
+        const int64_t r = r0 + (ci >> p.k4_log2);
         if (v && PINNED) {
-            R.p[c] = ld_pinned_cs(reinterpret_cast<const float4*>(p.prob + r * p.k) + ch);
-            R.c[c] = ld_pinned_cs(reinterpret_cast<const int4*>(p.col + r * p.k) + ch);
+            R.p[c] = ld_pinned_cs(reinterpret_cast<const float4*>(p.prob + e));
+            R.c[c] = ld_pinned_cs(reinterpret_cast<const int4*>(p.col + e));
             R.cost[c] = ld_pinned_nc(p.cost + r);
         } else if (v) {
-            R.p[c] = __ldcs(reinterpret_cast<const float4*>(p.prob + r * p.k) + ch);
-            R.c[c] = __ldcs(reinterpret_cast<const int4*>(p.col + r * p.k) + ch);
+            R.p[c] = __ldcs(reinterpret_cast<const float4*>(p.prob + e));
+            R.c[c] = __ldcs(reinterpret_cast<const int4*>(p.col + e));
             R.cost[c] = __ldg(p.cost + r);
         } else {
             R.p[c] = make_float4(0.f, 0.f, 0.f, 0.f);
