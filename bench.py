@@ -35,7 +35,7 @@ import mdpgen  # noqa: E402
 METRIC = "time-to-1e-6 residual and Bellman backups/s vs batch b; P-stream HBM GB/s"
 N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
-CSR_DRAM_BYTES_PER_STATE_PASS = (11167924480 + 10862336) / (21 * 262144)
+CSR_DRAM_BYTES_PER_STATE_PASS = (11167719000 + 10510336) / (21 * 262144)
 # batched launch: DRAM bytes (read + write) over the algorithmic row bytes, from one ncu capture of the
 # 256-MDP launch with every MDP capped at 20 sweeps (72.7081 GB + 0.1504 GB over 72.0046 GB)
 BATCHED_DRAM_PER_ALGO_BYTE = (72708093000 + 150380800) / 72004641408
@@ -308,7 +308,7 @@ def main():
     per_launch_bytes = [(s["sweeps"] + 1) * sweep_bytes(n, M_ACTIONS, K_SUCC) for s in stats]
     achieved = sum(per_launch_bytes) / (kernel_ms / 1e3) / 1e9
     # DRAM bytes per state and pass from one ncu capture of this kernel (n = 2^18, b = 65536, 20 sweeps
-    # + the greedy pass: 11.179 GB); the values stay in L2, so traffic scales with states x passes
+    # + the greedy pass: 11.178 GB); the values stay in L2, so traffic scales with states x passes
     traffic = statistics.mean((s["sweeps"] + 1) * n * CSR_DRAM_BYTES_PER_STATE_PASS for s in stats)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": traffic, "traffic_note": "ncu capture at n=2^18 scaled by states x passes",
