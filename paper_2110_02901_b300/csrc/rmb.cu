@@ -1164,6 +1164,8 @@ struct BatchPlan {
     double makespan;
 };
 
+constexpr double kAloneMargin = 1.2;
+
 bool try_makespan(const std::vector<ItemCost>& cs, const std::vector<int64_t>& fixed, int ctas, double eps, double M,
                   BatchPlan* out)
 {
@@ -1173,7 +1175,9 @@ bool try_makespan(const std::vector<ItemCost>& cs, const std::vector<int64_t>& f
     int used = 0;
     for (int i = 0; i < N; ++i) {
         const ItemPlan one = best_b(cs[i], 1, eps, fixed[i]);
-        if (one.t <= M) {
+        // an MDP must meet M with a margin: the long solves (single CTAs and groups) start with the
+        // launch, while every SM streams rows, and measured up to ~1.2x their estimates there
+        if (one.t * kAloneMargin <= M) {
             ip[i] = one;
             small.push_back(i);
             continue;
@@ -1181,7 +1185,7 @@ bool try_makespan(const std::vector<ItemCost>& cs, const std::vector<int64_t>& f
         bool ok = false;
         for (int G = 2; G <= ctas; G = G < 8 ? G + 1 : G + G / 4) {
             const ItemPlan pg = best_b(cs[i], G, eps, fixed[i]);
-            if (pg.t <= M) {
+            if (pg.t * kAloneMargin <= M) {
                 ip[i] = pg;
                 ok = true;
                 break;
