@@ -148,7 +148,8 @@ typedef struct {
    same sweep have already landed (chaotic relaxation; b is ignored).  One barrier per sweep keeps
    the stop test.  Converges to the same fixed point; trajectories are not reproducible. */
 #define RMB_FLAG_ASYNC 4
-/* rmb_vi picks a one-cluster solve for small MDPs with small batches: up to 16 CTAs of one thread-block
+/* rmb_vi, rmb_mpi and rmb_eval_policy pick a one-cluster solve for small MDPs with small batches (MB-MPI:
+   improvement passes and evaluation sweeps alike): up to 16 CTAs of one thread-block
    cluster each hold a copy of the values (and of the order) in shared memory, exchange every batch's
    new values through distributed shared memory and separate batches by the hardware cluster barrier
    instead of a grid-wide barrier through memory (stats->path = 4).  It is taken when n * 16 bytes fit

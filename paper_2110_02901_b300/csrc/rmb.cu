@@ -895,7 +895,9 @@ int solve(const Call& q)
     // row offsets fit (16 bytes per state), every batch fits the cluster's warps (<= 2 states each) and the solve
     // is the paper's plain form (sigma order, sweep-change stop, float32 rows).
     int cluster = 0;
-    if (q.mode == MODE_VI && O->grid_ctas == 0 && select == RMB_SELECT_PERMUTATION && rkind == RMB_RESIDUAL_SWEEP &&
+    const bool cluster_mode = q.mode == MODE_VI || q.mode == MODE_MPI ||
+                              (q.mode == MODE_EVAL && !(O->flags & RMB_FLAG_RAW_ROWS));
+    if (cluster_mode && O->grid_ctas == 0 && select == RMB_SELECT_PERMUTATION && rkind == RMB_RESIDUAL_SWEEP &&
         !(O->flags & (RMB_FLAG_ASYNC | RMB_FLAG_INJECT_BARRIER_STALL | RMB_FLAG_NO_CLUSTER)) && p.T >= 2 &&
         (M->format == RMB_CSR || p.p_dtype == RMB_P_F32) && !std::getenv("RMB_NO_CLUSTER")) {
         // dense rows of <= 2048 values (n % 4 == 0, m <= 16) are staged per warp: + 8 KB per warp

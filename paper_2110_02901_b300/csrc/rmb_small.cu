@@ -38,6 +38,7 @@ constexpr int kDenseAhead = 16;   // float4 chunks per lane staged ahead: dense 
 // the state is computed.
 struct Ahead {
     int s;
+    int a;         // the only action taken (evaluation sweeps: the policy's), or -1 for the minimum over all
     bool fast;
     long long rp;
     float c, pr;
@@ -199,7 +200,7 @@ struct SmallRun {
 
     // Q-factors of state s at the values A (shared memory): min (and arg-min, second smallest)
     template <bool ARG>
-    __device__ Best eval(int s, const float* A) const
+    __device__ Best eval(int s, const float* A, int a_only) const
     {
         const int lane = threadIdx.x & 31;
         const uint32_t nm1 = (uint32_t)(p.n - 1);
@@ -236,7 +237,8 @@ struct SmallRun {
                     float x = part[u];
                     for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
                     if (a0 + u < p.m) {
-                        const float c = __ldg(p.cost + (int64_t)s * p.m + a0 + u);
+                        float c = __ldg(p.cost + (int64_t)s * p.m + a0 + u);
+                        if (a_only >= 0 && a0 + u != a_only) c = kInf;
                         const Best cur = {c == kInf ? kInf : fmaf(p.gamma, x, c), a0 + u, kInf};
                         best = better(best, cur);
                     }
@@ -253,6 +255,7 @@ struct SmallRun {
         if (p.m < 32) {
             if (lane <= p.m) rp = __ldg(p.row_ptr + r0 + lane);
             if (lane < p.m) c = __ldg(p.cost + r0 + lane);
+            if (a_only >= 0 && lane != a_only) c = kInf;
             const long long E0 = __shfl_sync(0xffffffffu, rp, 0), E1 = __shfl_sync(0xffffffffu, rp, p.m);
             if (E1 - E0 <= 32) {
                 float x = 0.f;
@@ -281,7 +284,7 @@ struct SmallRun {
             float x = 0.f;
             for (long long e = e0 + lane; e < e1; e += 32) x = fmaf(__ldg(p.prob + e), A[min((uint32_t)__ldg(p.col + e), nm1)], x);
             for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-            const float cc = __ldg(p.cost + r);
+            const float cc = (a_only >= 0 && a != a_only) ? kInf : __ldg(p.cost + r);
             best = better(best, Best{cc == kInf ? kInf : fmaf(p.gamma, x, cc), a, kInf});
         }
         return best;
@@ -289,16 +292,24 @@ struct SmallRun {
 
     __device__ float* warp_stage() const { return stage + (size_t)(threadIdx.x >> 5) * (kDenseAhead * 128); }
 
-    // rows of state s ahead of its batch (s < 0: none); with_stage: this slot may use the staging area
-    __device__ void load(int s, Ahead& h, AheadVec<NC>& hv, bool with_stage) const
+    // rows of state s ahead of its batch (s < 0: none); with_stage: this slot may use the staging area;
+    // a_only >= 0: only that action is taken (the other rows get cost +inf, so the minimum over the
+    // rows is Q(s, a_only), the backup of B_{pi,b})
+    __device__ void load(int s, Ahead& h, AheadVec<NC>& hv, bool with_stage, int a_only) const
     {
         const int lane = threadIdx.x & 31;
         h.s = s;
+        h.a = a_only;
         h.fast = false;
         if (s < 0) return;
         if constexpr (NC > 0) {
             h.fast = true;
             fast_load<K_MIN, NC>(p, s, true, 32, lane, hv.R);
+            if (a_only >= 0) {
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+                    if (((c * 32 + lane) >> p.k4_log2) != a_only) hv.R.cost[c] = kInf;
+            }
             return;
         }
         if (p.path == PATH_DENSE) {
@@ -316,7 +327,7 @@ struct SmallRun {
                                  ::"r"((uint32_t)__cvta_generic_to_shared(dst + 4 * q)), "l"(P4 + q) : "memory");
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
-            h.c = lane < p.m ? __ldg(p.cost + (int64_t)s * p.m + lane) : kInf;
+            h.c = lane < p.m && (a_only < 0 || lane == a_only) ? __ldg(p.cost + (int64_t)s * p.m + lane) : kInf;
             return;
         }
         const int e0 = rofs[s], e1 = rofs[s + 1];
@@ -324,7 +335,7 @@ struct SmallRun {
         h.fast = true;
         const int64_t r0 = (int64_t)s * p.m;
         h.rp = lane <= p.m ? __ldg(p.row_ptr + r0 + lane) : 0;
-        h.c = lane < p.m ? __ldg(p.cost + r0 + lane) : kInf;
+        h.c = lane < p.m && (a_only < 0 || lane == a_only) ? __ldg(p.cost + r0 + lane) : kInf;
         h.pr = 0.f;
         h.col = 0;
         if (lane < e1 - e0) {
@@ -339,7 +350,7 @@ struct SmallRun {
     {
         const int lane = threadIdx.x & 31;
         if constexpr (NC > 0) return fast_eval<ARG, NC, VM_SHARED>(p, hv.R, A, 32, lane);
-        if (!h.fast) return eval<ARG>(h.s, A);
+        if (!h.fast) return eval<ARG>(h.s, A, h.a);
         Best cur = {kInf, 0x7fffffff, kInf};
         if (p.path == PATH_DENSE) {
             const int n4 = p.n >> 2;
@@ -511,9 +522,13 @@ struct SmallRun {
                 rofs[i] = (int32_t)min(__ldg(p.row_ptr + (int64_t)i * p.m), (int64_t)0x7fffffff);
         if (ok) compute_perm(p.start_sweep);
         __syncthreads();
-        long long sweeps = 0;
+        long long sweeps = 0, iters = 0;
         double residual = 0.0;
         bool converged = false;
+        const bool mpi = p.mode == MODE_MPI;
+        // sweeps of B_{pi,b} (MB-MPI's evaluation sweeps, policy evaluation) take the policy's row only
+        const bool pol_rows = p.mode != MODE_VI;
+        const int32_t* pol = p.pi_in ? p.pi_in : p.pi;
         // rows of this warp's states of the next batch, loaded between the arrival at and the wait on
         // the barrier before it (dense: the first slot uses the warp's staging area)
         Ahead ah[kSmallMaxPer];
@@ -523,19 +538,25 @@ struct SmallRun {
 #pragma unroll
             for (int r = 0; r < kSmallMaxPer; ++r) {
                 const int i = my_pos(r);
-                load(i < len ? order[t * p.b + i] : -1, ah[r], av[r], r == 0);
+                const int s = i < len ? order[t * p.b + i] : -1;
+                // the policy was written before a barrier this CTA has waited on (MB-MPI: the
+                // improvement pass), and is read at L2
+                const int a = (pol_rows && s >= 0) ? (int)min((uint32_t)ld_l2(pol + s), (uint32_t)(p.m - 1)) : -1;
+                load(s, ah[r], av[r], r == 0, a);
             }
         };
-        if (ok) prefetch(pbuf(p.start_sweep), 0);
         uint32_t bt = 0;   // batches done (list buffer parity)
-        for (long long j = 0; ok && j < p.max_sweeps; ++j) {
-            const long long k = p.start_sweep + j;
+        // sweep k over its order, whose first batch has been prefetched; next_sweep: the first batch of
+        // sweep k + 1 may be prefetched at the last barrier (not when a pass that changes the policy
+        // comes first).  Returns false on an error (the same in every CTA).
+        auto sweep = [&](long long k, bool next_sweep, float& delta, float& lo, float& hi) -> bool {
             const int32_t* order = pbuf(k);
             const int slot = red_epoch % 3;
             clear_slot((red_epoch + 1) % 3);
             ++red_epoch;
             Acc acc = {0.f, kInf, -kInf};
-            for (int t = 0; ok && t < p.T; ++t, ++bt) {
+            bool good = true;
+            for (int t = 0; good && t < p.T; ++t, ++bt) {
                 const int par = bt & 1;
 #pragma unroll
                 for (int r = 0; r < kSmallMaxPer; ++r) {
@@ -563,40 +584,121 @@ struct SmallRun {
                 // arrive: loads issued before a release arrival would hold it back until they complete
                 arrive();
                 if (t + 1 < p.T) prefetch(order, t + 1);
-                else prefetch(pbuf(k + 1), 0);
-                ok = wait();
-                if (ok) apply(par, batch_len(t));
+                else if (next_sweep) prefetch(pbuf(k + 1), 0);
+                good = wait();
+                if (good) apply(par, batch_len(t));
             }
-            if (!ok) break;
-            float delta, lo, hi;
+            if (!good) return false;
             read_slot(slot, delta, lo, hi);
-            ++sweeps;
-            residual = (double)delta;
-            if (rank == 0 && threadIdx.x == 0 && p.trace) p.trace[j] = residual;
-            if (delta != delta) {   // the same value in every CTA
-                if (rank == 0 && threadIdx.x == 0) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
-                ok = false;
-                break;
+            return true;
+        };
+        // MB-MPI's improvement pass (Alg. 1): the greedy policy and Q-gap at the current values, written
+        // by the CTA that owns the state's range, and ||TV - V||_inf over the cluster; V is unchanged
+        auto greedy_pass = [&](float& resid) -> bool {
+            const int slot = red_epoch % 3;
+            clear_slot((red_epoch + 1) % 3);
+            ++red_epoch;
+            Acc acc = {0.f, kInf, -kInf};
+            const uint32_t per = ((uint32_t)p.n + C - 1) / C;
+            const uint32_t lo = rank * per, hi = min((uint32_t)p.n, lo + per);
+            for (uint32_t i = lo + (threadIdx.x >> 5); i < hi; i += kSmallWarps) {
+                Ahead h;
+                AheadVec<NC> hv;
+                load((int)i, h, hv, false, -1);
+                const Best q = compute<true>(h, hv, V);
+                if (lane == 0) {
+                    const float d = new_value(q.q, Ce) - V[i];
+                    if (d != d) raise(RMB_ERR_NONFINITE);
+                    acc.dmax = fmaxf(acc.dmax, fabsf(d));
+                    st_l2(p.pi + i, q.a);
+                    if (p.qgap) p.qgap[i] = q.q2 - q.q;
+                }
             }
-            if ((double)delta <= p.eps) { converged = true; break; }
+            publish(slot, acc);
+            arrive();
+            const bool good = wait();
+            float l2, h2;
+            if (good) read_slot(slot, resid, l2, h2);
+            return good;
+        };
+        auto shift_values = [&](float lo, float hi) {
             const float sh = shift_for(lo, hi);
             if (sh != 0.f) {   // every CTA shifts its own copy; other CTAs read only its lists
                 for (int i = threadIdx.x; i < p.n; i += kSmallThreads) V[i] -= sh;
                 Ce = make_centre(Ce.mu + (double)sh, p.gamma_d);
                 __syncthreads();
             }
+        };
+        if (ok && !mpi) {
+            // MB-VI / policy evaluation: sweeps until the sweep change is <= eps
+            prefetch(pbuf(p.start_sweep), 0);
+            for (long long j = 0; ok && j < p.max_sweeps; ++j) {
+                float delta, lo, hi;
+                if (!sweep(p.start_sweep + j, true, delta, lo, hi)) {
+                    ok = false;
+                    break;
+                }
+                ++sweeps;
+                residual = (double)delta;
+                if (rank == 0 && threadIdx.x == 0 && p.trace) p.trace[j] = residual;
+                if (delta != delta) {   // the same value in every CTA
+                    if (rank == 0 && threadIdx.x == 0) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
+                    ok = false;
+                    break;
+                }
+                if ((double)delta <= p.eps) { converged = true; break; }
+                shift_values(lo, hi);
+            }
         }
-        // outputs: values, and the greedy policy / Q-gap at them (a full Bellman pass)
+        if (ok && mpi) {
+            // MB-MPI (Alg. 1): improvement pass, stop test, K sweeps of B_{pi,b}; the sweep counter of
+            // sigma runs on across the evaluation sweeps of all iterations
+            for (;;) {
+                float r = 0.f;
+                if (!greedy_pass(r)) {
+                    ok = false;
+                    break;
+                }
+                residual = (double)r;
+                if (rank == 0 && threadIdx.x == 0 && p.trace) p.trace[iters] = residual;
+                ++iters;
+                if (r != r) {
+                    if (rank == 0 && threadIdx.x == 0) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
+                    ok = false;
+                    break;
+                }
+                if (residual <= p.eps) { converged = true; break; }
+                if (iters >= p.max_sweeps) break;
+                prefetch(pbuf(p.start_sweep + sweeps), 0);
+                for (int e = 0; ok && e < p.K; ++e) {
+                    float delta, lo, hi;
+                    if (!sweep(p.start_sweep + sweeps, e + 1 < p.K, delta, lo, hi)) {
+                        ok = false;
+                        break;
+                    }
+                    ++sweeps;
+                    if (delta != delta) {
+                        if (rank == 0 && threadIdx.x == 0) atomicCAS(&p.ctrl->error, 0, RMB_ERR_NONFINITE);
+                        ok = false;
+                        break;
+                    }
+                    shift_values(lo, hi);
+                }
+                if (!ok) break;
+            }
+        }
+        // outputs: values, and (MB-VI) the greedy policy / Q-gap at them (a full Bellman pass); MB-MPI's
+        // last improvement pass wrote its policy and Q-gap already
         if (ok) {
             const uint32_t per = ((uint32_t)p.n + C - 1) / C;
             const uint32_t lo = rank * per, hi = min((uint32_t)p.n, lo + per);
             for (uint32_t i = lo + threadIdx.x; i < hi; i += kSmallThreads) p.Vout[i] = (float)(Ce.mu + (double)V[i]);
-            if (p.pi || p.qgap) {
+            if (!mpi && (p.pi || p.qgap)) {
                 for (uint32_t i = lo + (threadIdx.x >> 5); i < hi; i += kSmallWarps) {
                     Ahead h;
                     AheadVec<NC> hv;
-                    if constexpr (NC > 0) load((int)i, h, hv, false);
-                    const Best q = NC > 0 ? compute<true>(h, hv, V) : eval<true>((int)i, V);
+                    load((int)i, h, hv, false, -1);
+                    const Best q = compute<true>(h, hv, V);
                     if (lane == 0) {
                         if (p.pi) p.pi[i] = q.a;
                         if (p.qgap) p.qgap[i] = q.q2 - q.q;
@@ -608,7 +710,7 @@ struct SmallRun {
         if (rank == 0 && threadIdx.x == 0) {
             Ctrl* c = p.ctrl;
             c->sweeps = sweeps;
-            c->iters = 0;
+            c->iters = iters;
             c->barriers = syncs;
             c->residual = residual;
             c->mu = Ce.mu;

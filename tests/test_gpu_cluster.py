@@ -141,8 +141,81 @@ def test_cluster_is_not_taken_outside_its_scope():
               rmb.Opts(batch=100, eps=0.0, max_sweeps=2, residual_kind=rmb.RMB_RESIDUAL_BELLMAN),
               rmb.Opts(batch=100, eps=0.0, max_sweeps=2, flags=rmb.RMB_FLAG_NO_CLUSTER)):
         assert rmb.rmb_vi(dm, o, V, check=False)[1]["path"] != "cluster"
-    assert rmb.rmb_mpi(dm, rmb.Opts(batch=100, eps=0.0, max_sweeps=2), V, pi, check=False)[1]["path"] != "cluster"
+    assert rmb.rmb_mpi(dm, rmb.Opts(batch=100, eps=0.0, max_sweeps=2, flags=rmb.RMB_FLAG_NO_CLUSTER), V, pi,
+                       check=False)[1]["path"] != "cluster"
     big = mdpgen.csr_uniform_k(15000, 2, 4, gamma=0.9, seed=15)        # 16 bytes per state do not fit
     V = torch.zeros(big.n, dtype=torch.float32, device="cuda")
     assert rmb.rmb_vi(rmb.DeviceMDP.from_host(big), rmb.Opts(batch=100, eps=0.0, max_sweeps=1), V,
                       check=False)[1]["path"] != "cluster"
+
+
+MPI_CASES = [c for c in CASES if c[0] in ("dense m=11", "csr k=32", "csr ragged", "csr >32 per state", "maze")]
+
+
+@pytest.mark.parametrize("name,make", MPI_CASES, ids=[c[0] for c in MPI_CASES])
+def test_cluster_mpi_matches_oracle_per_iteration(name, make):
+    """MB-MPI (Alg. 1) on the cluster: improvement pass (greedy policy at V, ||TV - V||_inf), then K
+    sweeps of B_{pi,b} (eq. (12)) over sigma with the sweep counter running on; values after 1 and 3
+    outer iterations, the last residual and the policy equal the oracle's MB-MPI, and the grid solve's."""
+    mdp = make()
+    dm = rmb.DeviceMDP.from_host(mdp)
+    V0 = mdpgen.random_values(mdp.n, seed=8) * 2
+    for b, K in ((7, 3), (64, 2)):
+        for iters in (1, 3):
+            ref = oracle.mpi(mdp, b, K, seed=23, eps=0.0, max_iters=iters, V0=V0, start_sweep=1)
+            out = {}
+            for flags in (0, rmb.RMB_FLAG_NO_CLUSTER):
+                V = torch.from_numpy(V0).cuda()
+                pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
+                gap = torch.empty(mdp.n, dtype=torch.float32, device="cuda")
+                st = rmb.rmb_mpi(dm, rmb.Opts(batch=b, seed=23, eps=0.0, max_sweeps=iters, eval_sweeps=K,
+                                              start_sweep=1, flags=flags), V, pi, gap)
+                assert (st["path"] == "cluster") == (flags == 0), (flags, st)
+                assert st["iters"] == iters and st["sweeps"] == K * (iters - 1), (b, K, iters, st)
+                close(V.cpu().numpy(), ref["V"])
+                close([st["residual"]], np.array([ref["resid"][-1]]), tol=1e-5)
+                out[flags] = (V.cpu().numpy(), pi.cpu().numpy(), gap.cpu().numpy())
+            # the policy of the last improvement pass where it is not a near tie
+            Vc, pic, gapc = out[0]
+            sel = gapc > 1e-5 * max(1.0, float(np.abs(Vc).max()))
+            assert np.array_equal(pic[sel], ref["pi"][sel])
+            close(out[0][0], out[rmb.RMB_FLAG_NO_CLUSTER][0])
+
+
+def test_cluster_mpi_converges_to_the_optimum():
+    mdp = mdpgen.csr_uniform_k(3000, 6, 16, gamma=0.97, seed=31)
+    dm = rmb.DeviceMDP.from_host(mdp)
+    jstar, pistar, _ = exact.policy_iteration(mdp)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
+    st = rmb.rmb_mpi(dm, rmb.Opts(batch=128, seed=6, eps=1e-6, max_sweeps=100000, eval_sweeps=10), V, pi)
+    assert st["status"] == rmb.RMB_OK and st["path"] == "cluster"
+    close(V.cpu().numpy(), jstar)
+    _, _, jgap, _ = exact.bellman_pass(mdp, jstar)
+    sel = jgap > 1e-6 * max(1.0, float(np.abs(jstar).max()))
+    assert np.array_equal(pi.cpu().numpy()[sel], pistar[sel])
+
+
+EVAL_CASES = [c for c in CASES if c[0] in ("dense n%4", "dense m=11", "csr k=32", "csr >32 per state", "csr m=40")]
+
+
+@pytest.mark.parametrize("name,make", EVAL_CASES, ids=[c[0] for c in EVAL_CASES])
+def test_cluster_policy_evaluation_matches_oracle(name, make):
+    """Sweeps of B_{pi,b} (eq. (12)) for a fixed policy on the cluster: trajectories equal the oracle's;
+    converged values equal J_pi (eq. (4), a direct solve)."""
+    mdp = make()
+    dm = rmb.DeviceMDP.from_host(mdp)
+    pi = mdpgen.random_policy(mdp.n, mdp.m, seed=5)
+    pit = torch.from_numpy(pi).cuda()
+    V0 = mdpgen.random_values(mdp.n, seed=4)
+    for b in (5, 100):
+        ref = oracle.eval_policy(mdp, pi, b, seed=12, eps=0.0, max_sweeps=4, V0=V0)
+        V = torch.from_numpy(V0).cuda()
+        st = rmb.rmb_eval_policy(dm, pit, rmb.Opts(batch=b, seed=12, eps=0.0, max_sweeps=4), V, check=False)[1]
+        assert st["path"] == "cluster" and st["sweeps"] == 4, (b, st)
+        close(V.cpu().numpy(), ref["V"])
+    J = exact.policy_value(mdp, pi)
+    V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
+    st = rmb.rmb_eval_policy(dm, pit, rmb.Opts(batch=64, seed=4, eps=1e-7, max_sweeps=100000), V)
+    assert st["status"] == rmb.RMB_OK and st["path"] == "cluster"
+    close(V.cpu().numpy(), J)
