@@ -195,8 +195,9 @@ def test_dense_paths(n, m, stage, monkeypatch):
 
 
 # ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("flags", [0, rmb.RMB_FLAG_NO_CLUSTER], ids=["auto", "grid"])
 @pytest.mark.parametrize("fmt", ["csr", "dense"])
-def test_policy_evaluation_parity_and_closed_form(fmt):
+def test_policy_evaluation_parity_and_closed_form(fmt, flags):
     mdp = (mdpgen.csr_uniform_k(3000, 8, 32, gamma=0.97, seed=21) if fmt == "csr"
            else mdpgen.dense_dirichlet(600, 4, gamma=0.95, seed=22))
     dm = rmb.DeviceMDP.from_host(mdp)
@@ -205,8 +206,9 @@ def test_policy_evaluation_parity_and_closed_form(fmt):
     for b in (1, 100, mdp.n):
         ref = oracle.eval_policy(mdp, pi, b, seed=4, eps=0.0, max_sweeps=5, traj=True)
         V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
-        st = rmb.rmb_eval_policy(dm, pit, rmb.Opts(batch=b, seed=4, eps=0.0, max_sweeps=5), V)
+        st = rmb.rmb_eval_policy(dm, pit, rmb.Opts(batch=b, seed=4, eps=0.0, max_sweeps=5, flags=flags), V)
         assert st["sweeps"] == 5
+        assert (st["path"] == "cluster") == (flags == 0 and b < mdp.n), (b, st["path"])
         close(to_np(V), ref["traj"][4])
     J = exact.policy_value(mdp, pi)
     V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
@@ -215,8 +217,9 @@ def test_policy_evaluation_parity_and_closed_form(fmt):
     close(to_np(V), J)
 
 
+@pytest.mark.parametrize("flags", [0, rmb.RMB_FLAG_NO_CLUSTER], ids=["auto", "grid"])
 @pytest.mark.parametrize("fmt", ["csr", "dense"])
-def test_mpi_parity(fmt):
+def test_mpi_parity(fmt, flags):
     mdp = (mdpgen.csr_uniform_k(4000, 8, 32, gamma=0.99, seed=31) if fmt == "csr"
            else mdpgen.dense_dirichlet(500, 4, gamma=0.95, seed=32))
     dm = rmb.DeviceMDP.from_host(mdp)
@@ -225,14 +228,14 @@ def test_mpi_parity(fmt):
             ref = oracle.mpi(mdp, b, K, seed=6, eps=0.0, max_iters=iters)
             V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
             pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
-            st = rmb.rmb_mpi(dm, rmb.Opts(batch=b, seed=6, eps=0.0, max_sweeps=iters, eval_sweeps=K), V, pi)
+            st = rmb.rmb_mpi(dm, rmb.Opts(batch=b, seed=6, eps=0.0, max_sweeps=iters, eval_sweeps=K, flags=flags), V, pi)
             assert st["iters"] == iters and st["sweeps"] == K * (iters - 1)
             close(to_np(V), ref["V"])
             close([st["residual"]], np.array([ref["resid"][-1]]), rtol=1e-5)
     jstar, pistar, _ = exact.policy_iteration(mdp)
     V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
     pi = torch.empty(mdp.n, dtype=torch.int32, device="cuda")
-    st = rmb.rmb_mpi(dm, rmb.Opts(batch=64, seed=6, eps=1e-6, max_sweeps=100000, eval_sweeps=10), V, pi)
+    st = rmb.rmb_mpi(dm, rmb.Opts(batch=64, seed=6, eps=1e-6, max_sweeps=100000, eval_sweeps=10, flags=flags), V, pi)
     assert st["status"] == rmb.RMB_OK
     close(to_np(V), jstar)
     _, _, jgap, _ = exact.bellman_pass(mdp, jstar)
