@@ -132,3 +132,33 @@ def test_batched_full_config_against_single_solves_and_oracle():
         ref = oracle.mbvi(mdps[i], plan[i]["batch"], seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000)
         v = Vs[i].cpu().numpy().astype(np.float64)
         assert np.max(np.abs(v - ref["V"])) <= 1e-5 * max(1.0, np.abs(ref["V"]).max()), i
+
+
+def test_batched_groups_with_shared_memory_values_odd_batch_counts():
+    """MDPs solved by a group of CTAs, each with a copy of the values in shared memory: three batches
+    per sweep (the two (state, value) lists alternate across sweeps as well), one MDP whose values
+    exceed shared memory (the states past 57344 in L2), start values away from zero (re-centring) and
+    greedy outputs; values, policies and sweep counts equal rmb_vi's bit for bit."""
+    mdps = [mdpgen.csr_uniform_k(30000, 8, 16, gamma=0.97, seed=41),
+            mdpgen.csr_uniform_k(70000, 4, 16, gamma=0.95, seed=42)]
+    bs = [10001, 23334]
+    dms = [rmb.DeviceMDP.from_host(m) for m in mdps]
+    V0 = [mdpgen.random_values(m.n, seed=43 + i, scale=0.5, offset=20.0) for i, m in enumerate(mdps)]
+    Vs = [torch.from_numpy(v).cuda() for v in V0]
+    pis = [torch.empty(m.n, dtype=torch.int32, device="cuda") for m in mdps]
+    opts = rmb.Opts(batch=1, seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000)
+    B = rmb.Batch(dms, Vs, opts, pis=pis, batches=bs)
+    plan = B.plan_table()
+    assert [p["batch"] for p in plan] == bs
+    assert all(p["group_ctas"] > 1 for p in plan), plan
+    B.run()
+    res = B.results()
+    assert all(r["status"] == rmb.RMB_OK for r in res)
+    for i, dm in enumerate(dms):
+        V1 = torch.from_numpy(V0[i]).cuda()
+        pi1 = torch.empty(mdps[i].n, dtype=torch.int32, device="cuda")
+        st = rmb.rmb_vi(dm, rmb.Opts(batch=bs[i], seed=mdpgen.PERM_SEED, eps=1e-6, max_sweeps=200000,
+                                     flags=rmb.RMB_FLAG_NO_CLUSTER), V1, pi1)
+        assert st["sweeps"] == res[i]["sweeps"], i
+        assert torch.equal(V1, Vs[i]), i
+        assert torch.equal(pi1, pis[i]), i
