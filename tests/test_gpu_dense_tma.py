@@ -71,13 +71,16 @@ def test_tma_mpi_and_evaluation(storage):
     ref = oracle.mpi(ref_mdp, 128, K=5, seed=3, eps=0.0, max_iters=3)
     V = torch.zeros(n, dtype=torch.float32, device="cuda")
     pi = torch.empty(n, dtype=torch.int32, device="cuda")
-    st = rmb.rmb_mpi(form, rmb.Opts(batch=128, seed=3, eps=0.0, max_sweeps=3, eval_sweeps=5), V, pi)
+    st = rmb.rmb_mpi(form, rmb.Opts(batch=128, seed=3, eps=0.0, max_sweeps=3, eval_sweeps=5,
+                                    flags=rmb.RMB_FLAG_NO_CLUSTER), V, pi)
     assert st["path"] == "dense-tma" and st["iters"] == 3
     close(V.cpu().numpy(), ref["V"])
     pol = mdpgen.random_policy(n, m, seed=4)
     ev = oracle.eval_policy(ref_mdp, pol, 300, seed=8, eps=0.0, max_sweeps=4)
     V2 = torch.zeros(n, dtype=torch.float32, device="cuda")
-    st = rmb.rmb_eval_policy(form, torch.from_numpy(pol).cuda(), rmb.Opts(batch=300, seed=8, eps=0.0, max_sweeps=4), V2)
+    st = rmb.rmb_eval_policy(form, torch.from_numpy(pol).cuda(),
+                             rmb.Opts(batch=300, seed=8, eps=0.0, max_sweeps=4, flags=rmb.RMB_FLAG_NO_CLUSTER), V2)
+    assert st["path"] == "dense-tma"
     close(V2.cpu().numpy(), ev["V"])
 
 

@@ -212,7 +212,7 @@ def test_policy_evaluation_parity_and_closed_form(fmt, flags):
         close(to_np(V), ref["traj"][4])
     J = exact.policy_value(mdp, pi)
     V = torch.zeros(mdp.n, dtype=torch.float32, device="cuda")
-    st = rmb.rmb_eval_policy(dm, pit, rmb.Opts(batch=128, seed=4, eps=1e-7, max_sweeps=100000), V)
+    st = rmb.rmb_eval_policy(dm, pit, rmb.Opts(batch=128, seed=4, eps=1e-7, max_sweeps=100000, flags=flags), V)
     assert st["status"] == rmb.RMB_OK
     close(to_np(V), J)
 
