@@ -358,15 +358,30 @@ struct SmallRun {
             __syncwarp();
             const float4* st4 = reinterpret_cast<const float4*>(warp_stage());
             const float4* A4 = reinterpret_cast<const float4*>(A);
-            for (int a = 0; a < p.m; ++a) {   // row a of the state is staged at chunks [a n4, (a+1) n4)
-                float part = 0.f;
+            // row a of the state is staged at chunks [a n4, (a+1) n4); four rows at a time, so that
+            // their loads and their warp sums overlap
+            for (int a0 = 0; a0 < p.m; a0 += 4) {
+                float part[4] = {0.f, 0.f, 0.f, 0.f};
                 for (int j4 = lane; j4 < n4; j4 += 32) {
-                    const float4 pv = st4[a * n4 + j4], av = A4[j4];
-                    part = fmaf(pv.x, av.x, fmaf(pv.y, av.y, fmaf(pv.z, av.z, fmaf(pv.w, av.w, part))));
+                    const float4 av = A4[j4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        if (a0 + u < p.m) {
+                            const float4 pv = st4[(a0 + u) * n4 + j4];
+                            part[u] = fmaf(pv.x, av.x, fmaf(pv.y, av.y, fmaf(pv.z, av.z, fmaf(pv.w, av.w, part[u]))));
+                        }
+                    }
                 }
-                for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-                const float c = __shfl_sync(0xffffffffu, h.c, a);
-                cur = better(cur, Best{c == kInf ? kInf : fmaf(p.gamma, part, c), a, kInf});
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) part[u] += __shfl_xor_sync(0xffffffffu, part[u], off);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float c = __shfl_sync(0xffffffffu, h.c, (a0 + u) & 31);
+                    if (a0 + u < p.m) cur = better(cur, Best{c == kInf ? kInf : fmaf(p.gamma, part[u], c), a0 + u, kInf});
+                }
             }
             return cur;
         }
