@@ -37,8 +37,8 @@ N_STATES, M_ACTIONS, K_SUCC, GAMMA = 1 << 20, 8, 32, 0.99
 EPS = 1e-6
 CSR_DRAM_BYTES_PER_STATE_PASS = (11167719000 + 10510336) / (21 * 262144)
 # batched launch: DRAM bytes (read + write) over the algorithmic row bytes, from one ncu capture of the
-# 256-MDP launch with every MDP capped at 20 sweeps (72.7081 GB + 0.1504 GB over 72.0046 GB)
-BATCHED_DRAM_PER_ALGO_BYTE = (72708093000 + 150380800) / 72004641408
+# 256-MDP launch with every MDP capped at 20 sweeps (72.6275 GB + 0.1440 GB over 72.0046 GB)
+BATCHED_DRAM_PER_ALGO_BYTE = (72627516000 + 144032512) / 72004641408
 DENSE_DRAM_BYTES_PER_P_BYTE = (4285076000 + 7139328) / (4 * 4096 * 16 * 4096 * 4)
 B_SWEEP = [1024, 16384, 262144, 1 << 20]
 HEADLINE_B = 262144
@@ -905,7 +905,7 @@ def _batched(args, world, rmb, torch, stream, hbm, peak_kind):
                            "frac": nnz_passes / (ms / 1e3) / 1e9 / hbm,
                            "traffic": BATCHED_DRAM_PER_ALGO_BYTE * nnz_passes,
                            "traffic_note": "ncu DRAM bytes / algorithmic bytes of the same launch capped at 20 "
-                                           "sweeps per MDP (1.012), times this run's algorithmic bytes",
+                                           "sweeps per MDP (1.011), times this run's algorithmic bytes",
                            "kernel": "rmb_batched_kernel", "peak_kind": peak_kind},
                  cpu_baseline=cpu)
 
