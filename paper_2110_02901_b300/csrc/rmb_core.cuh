@@ -504,28 +504,7 @@ struct Carry {
     bool valid;
 };
 
-// Row loads that keep their place in the program: volatile, so the compiler issues them where they are
-// written (ahead of the gathers of earlier steps) instead of next to their first use.
-__device__ __forceinline__ float4 ld_pinned_cs(const float4* a)
-{
-    float4 v;
-    asm volatile("ld.global.cs.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(a));
-    return v;
-}
-__device__ __forceinline__ int4 ld_pinned_cs(const int4* a)
-{
-    int4 v;
-    asm volatile("ld.global.cs.v4.s32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(a));
-    return v;
-}
-__device__ __forceinline__ float ld_pinned_nc(const float* a)
-{
-    float v;
-    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(a));
-    return v;
-}
-
-template <int KIND, int NC, bool PINNED = false>
+template <int KIND, int NC>
 __device__ __forceinline__ void fast_load(const KP& p, int s, bool act, int lps, int lane_g, StateRegs<NC>& R)
 {
     int pi_s = -1;
@@ -542,11 +521,7 @@ __device__ __forceinline__ void fast_load(const KP& p, int s, bool act, int lps,
         const bool v = act && ci < total;
         const int64_t e = e0 + 4 * ci;
         const int64_t r = r0 + (ci >> p.k4_log2);
-        if (v && PINNED) {
-            R.p[c] = ld_pinned_cs(reinterpret_cast<const float4*>(p.prob + e));
-            R.c[c] = ld_pinned_cs(reinterpret_cast<const int4*>(p.col + e));
-            R.cost[c] = ld_pinned_nc(p.cost + r);
-        } else if (v) {
+        if (v) {
             R.p[c] = __ldcs(reinterpret_cast<const float4*>(p.prob + e));
             R.c[c] = __ldcs(reinterpret_cast<const int4*>(p.col + e));
             R.cost[c] = __ldg(p.cost + r);
@@ -1894,11 +1869,11 @@ struct SoloRun {
         int s_cur = step_state(G, 0, pos0, len, K, bs, bs_j0);
         int s_n1 = step_state(G, 1, pos0, len, K, bs, bs_j0);
         StateRegs<NCA> cur, n1, n2;
-        fast_load<K_MIN, NCA, true>(p, s_cur < 0 ? 0 : s_cur, s_cur >= 0, lps, G.lane_g, cur);
-        fast_load<K_MIN, NCA, true>(p, s_n1 < 0 ? 0 : s_n1, s_n1 >= 0, lps, G.lane_g, n1);
+        fast_load<K_MIN, NCA>(p, s_cur < 0 ? 0 : s_cur, s_cur >= 0, lps, G.lane_g, cur);
+        fast_load<K_MIN, NCA>(p, s_n1 < 0 ? 0 : s_n1, s_n1 >= 0, lps, G.lane_g, n1);
         for (int j = 0; G.first + j * G.U < len; ++j) {
             const int s_n2 = step_state(G, j + 2, pos0, len, K, bs, bs_j0);
-            fast_load<K_MIN, NCA, true>(p, s_n2 < 0 ? 0 : s_n2, s_n2 >= 0, lps, G.lane_g, n2);
+            fast_load<K_MIN, NCA>(p, s_n2 < 0 ? 0 : s_n2, s_n2 >= 0, lps, G.lane_g, n2);
             const Best r = SPLIT ? fast_eval<ARG, NCA, VM_SPLIT>(p, cur, Vs, lps, G.lane_g, Hs, nsm)
                                  : fast_eval<ARG, NCA, VM_SHARED>(p, cur, Vs, lps, G.lane_g);
             if (s_cur >= 0 && G.lane_g == 0) {
