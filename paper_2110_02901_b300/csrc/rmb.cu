@@ -49,8 +49,8 @@ __global__ void rmb_tr_count_kernel(int n, int m, int k, const int32_t* __restri
 }
 
 // exclusive scan of the counts into row_ptr (one CTA: runs once per gradient call)
-__global__ void rmb_tr_scan_kernel(int n, const int32_t* __restrict__ cnt, int64_t* __restrict__ row_ptr,
-                                   int32_t* __restrict__ cursor)
+// cursor may be cnt itself (the counts become the scatter cursors), so neither is declared __restrict__
+__global__ void rmb_tr_scan_kernel(int n, const int32_t* cnt, int64_t* __restrict__ row_ptr, int32_t* cursor)
 {
     __shared__ int64_t part[1024];
     const int T = blockDim.x, t = threadIdx.x;
@@ -831,8 +831,8 @@ int solve(const Call& q)
     p.qgap = q.qgap;
     p.pi_in = q.pi_in;
 
-    const void* fn;
-    int threads, per_sm;
+    const void* fn = nullptr;
+    int threads = 0, per_sm = 0;
     size_t smem = 0;
     if (path == PATH_DENSE) {
         // large rows stream through the TMA pipeline when the staged values and the ring fit
