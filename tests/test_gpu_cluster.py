@@ -197,6 +197,8 @@ def test_cluster_mpi_converges_to_the_optimum():
 
 
 EVAL_CASES = [c for c in CASES if c[0] in ("dense n%4", "dense m=11", "csr k=32", "csr >32 per state", "csr m=40")]
+# rows staged per warp by cp.async (m n <= 2048, n % 4 == 0): the policy's row is picked by its cost
+EVAL_CASES.append(("dense staged", lambda: mdpgen.dense_dirichlet(500, 4, gamma=0.95, seed=7)))
 
 
 @pytest.mark.parametrize("name,make", EVAL_CASES, ids=[c[0] for c in EVAL_CASES])
