@@ -411,7 +411,15 @@ def main():
     if rank == 0 and not args.no_configs:
         del dm, ws
         torch.cuda.empty_cache()
-        cfgs = configs_summary(args, rmb, torch, stream, hbm, peak_kind)
+        try:
+            cfgs = configs_summary(args, rmb, torch, stream, hbm, peak_kind)
+        except Exception as e:   # the headline line is printed whatever happens to the other workloads
+            cfgs = {"error": f"{type(e).__name__}: {e}"[:400]}
+            try:
+                torch.cuda.synchronize()
+                torch.cuda.empty_cache()
+            except Exception:
+                pass
 
     total_launches = rmb.rmb_kernel_launches() - launches0
     if rank == 0:
