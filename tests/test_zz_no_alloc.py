@@ -7,7 +7,6 @@ takes no workspace: its scratch is a fixed array inside the library.  These test
 the C ABI and compare it with rmb_vi (which takes a caller-provided workspace), on consecutive calls
 so that whatever the previous call left in the shared array is exercised.
 """
-import ctypes
 
 import numpy as np
 import pytest
